@@ -1,0 +1,265 @@
+"""FP64 CPU oracle for the illumination decomposition solve (test infrastructure).
+
+TEST INFRASTRUCTURE ONLY: imported by ``tests/``, by ``__graft_entry__.smoke()``
+and by the benchmark's CPU-baseline leg, never by the product library.  The
+arithmetic lives in ``oracle.c`` (plain serial FP64 C); this module compiles it
+with gcc, marshals numpy arrays through ctypes and adds the two steps the paper
+runs outside the GPU solver: the small base-colour solve by SVD (Sec. 6.1) and
+the outer flip-flop loop that alternates the Gauss-Newton step on the layers with
+the base-colour step (Sec. 6.1, sparse-dense splitting).
+
+Parity pins: see ``tests/test_oracle_*.py``.  The consistency prior of Sec. 5.1
+is defined in the paper only by citation, so its reading here is "parity
+unpinned" against the paper (only internal checks: finite-difference Jacobian,
+symmetry, zero residual for constant r).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+
+TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness", "non_neg")
+ALL = 0xFF
+
+# Fixed parameter set of Sec. 7 ("Parameters"), eps of Sec. 5.3.1, sharpness 50 of Sec. 5.2.
+DEFAULT_WEIGHTS = dict(
+    lambda_data=5000.0, lambda_clustering=200.0, lambda_rsparsity=20.0, p=1.0,
+    lambda_rconsistency=10.0, lambda_monochrome=10.0, lambda_isparsity=3.0,
+    lambda_smoothness=3.0, lambda_nonneg=1000.0, lambda_IR=10.0, lambda_CR=100.0,
+    eps=0.002, retinex_sharpness=50.0, tau=0.05, nonneg_strict=1, irls_half=0, rcluster_follows_b=0,
+)
+
+
+def build(force: bool = False) -> str:
+    """Compile oracle.c into liboracle.so (gcc, -O2, strict IEEE: no -ffast-math)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        D = ctypes.POINTER(ctypes.c_double)
+        P = ctypes.c_void_p
+        _lib.or_apply.argtypes = [P, D, D, ctypes.c_uint, D, D]
+        _lib.or_rhs.argtypes = [P, D, D, ctypes.c_uint, D]
+        _lib.or_diag.argtypes = [P, D, D, ctypes.c_uint, D]
+        _lib.or_surrogate.argtypes = [P, D, D, ctypes.c_uint, D]
+        _lib.or_residuals.argtypes = [P, D, D, ctypes.c_uint, D, ctypes.POINTER(ctypes.c_int), ctypes.c_long]
+        _lib.or_residuals.restype = ctypes.c_long
+        _lib.or_energy.argtypes = [P, D, D]
+        _lib.or_pcg.argtypes = [P, D, ctypes.c_int, D, D]
+        _lib.or_gn_step.argtypes = [P, D, ctypes.c_int]
+        _lib.or_dense_normal.argtypes = [P, D, D, D]
+        _lib.or_init_cold.argtypes = [P, D]
+        _lib.or_precompute.argtypes = [ctypes.c_int, ctypes.c_int, D, D, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
+                                       D, D, D, D]
+    return _lib
+
+
+class _Struct(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int), ("W", ctypes.c_int), ("K", ctypes.c_int)] + [
+        (n, ctypes.c_double) for n in (
+            "lambda_data", "lambda_clustering", "lambda_rsparsity", "p", "lambda_rconsistency",
+            "lambda_monochrome", "lambda_isparsity", "lambda_smoothness", "lambda_nonneg",
+            "lambda_IR", "lambda_CR", "eps")
+    ] + [
+        ("nonneg_strict", ctypes.c_int), ("irls_half", ctypes.c_int),
+        ("n_spatial", ctypes.c_int), ("n_temporal", ctypes.c_int),
+        ("off_spatial", ctypes.c_void_p), ("off_temporal", ctypes.c_void_p),
+        ("I", ctypes.c_void_p), ("labels", ctypes.c_void_p), ("b", ctypes.c_void_p),
+        ("wsr", ctypes.c_void_p), ("omega_s", ctypes.c_void_p), ("omega_t", ctypes.c_void_p),
+        ("rprev", ctypes.c_void_p), ("b_init", ctypes.c_void_p), ("rcluster_follows_b", ctypes.c_int),
+    ]
+
+
+def _d(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def precompute(I, off_s, off_t=None, Iprev=None, tau=0.05, sharpness=50.0):
+    """Per-frame inputs of the priors: C, w_SR, spatial and temporal pair weights."""
+    I = _f64(I)
+    _, H, W = I.shape
+    off_s = np.ascontiguousarray(off_s, dtype=np.int32).reshape(-1, 2)
+    off_t = np.zeros((0, 2), np.int32) if off_t is None else np.ascontiguousarray(off_t, dtype=np.int32).reshape(-1, 2)
+    C = np.zeros((3, H, W))
+    wsr = np.zeros((H, W))
+    om_s = np.zeros((len(off_s), H, W))
+    om_t = np.zeros((len(off_t), H, W))
+    ip = _f64(Iprev) if Iprev is not None else None
+    ci = ctypes.POINTER(ctypes.c_int)
+    lib().or_precompute(H, W, _d(I), _d(ip) if ip is not None else None, len(off_s), off_s.ctypes.data_as(ci),
+                        len(off_t), off_t.ctypes.data_as(ci), tau, sharpness, _d(C), _d(wsr), _d(om_s),
+                        _d(om_t) if ip is not None else None)
+    return C, wsr, om_s, (om_t if ip is not None else None)
+
+
+class Problem:
+    """One frame's decomposition problem; owns the arrays the C struct points to."""
+
+    def __init__(self, I, labels, b_init, wsr, omega_s, off_s, omega_t=None, off_t=None, rprev=None, b=None,
+                 **weights):
+        """b_init: the clustered base colours (anchor of the refinement and of
+        R_cluster); b: the current (refined) colours, default b_init."""
+        w = dict(DEFAULT_WEIGHTS)
+        w.update(weights)
+        self.weights = w
+        self.I = _f64(I)
+        _, self.H, self.W = self.I.shape
+        self.labels = np.ascontiguousarray(labels, dtype=np.uint8)
+        self.b_init = _f64(b_init).copy()
+        self.b = self.b_init.copy() if b is None else _f64(b).copy()
+        self.K = self.b.shape[0]
+        self.V = self.K + 4
+        self.wsr = _f64(wsr)
+        self.off_s = np.ascontiguousarray(off_s, dtype=np.int32).reshape(-1, 2)
+        self.omega_s = _f64(omega_s)
+        self.temporal = omega_t is not None and rprev is not None
+        self.off_t = np.ascontiguousarray(off_t if off_t is not None else np.zeros((0, 2)), dtype=np.int32).reshape(-1, 2)
+        self.omega_t = _f64(omega_t) if self.temporal else None
+        self.rprev = _f64(rprev) if self.temporal else None
+        s = _Struct()
+        s.H, s.W, s.K = self.H, self.W, self.K
+        for n in ("lambda_data", "lambda_clustering", "lambda_rsparsity", "p", "lambda_rconsistency",
+                  "lambda_monochrome", "lambda_isparsity", "lambda_smoothness", "lambda_nonneg",
+                  "lambda_IR", "lambda_CR", "eps"):
+            setattr(s, n, float(w[n]))
+        s.nonneg_strict, s.irls_half = int(w["nonneg_strict"]), int(w["irls_half"])
+        s.n_spatial, s.n_temporal = len(self.off_s), (len(self.off_t) if self.temporal else 0)
+        s.off_spatial, s.off_temporal = self.off_s.ctypes.data, self.off_t.ctypes.data
+        s.I, s.labels, s.b = self.I.ctypes.data, self.labels.ctypes.data, self.b.ctypes.data
+        s.wsr, s.omega_s = self.wsr.ctypes.data, self.omega_s.ctypes.data
+        s.omega_t = self.omega_t.ctypes.data if self.temporal else None
+        s.rprev = self.rprev.ctypes.data if self.temporal else None
+        s.b_init = self.b_init.ctypes.data
+        s.rcluster_follows_b = int(w["rcluster_follows_b"])
+        self._s = s
+
+    @property
+    def ptr(self):
+        return ctypes.byref(self._s)
+
+    @property
+    def shape(self):
+        return (self.V, self.H, self.W)
+
+    def set_b(self, b):
+        self.b[...] = b
+
+    def _x(self, X):
+        X = _f64(X)
+        assert X.shape == self.shape, (X.shape, self.shape)
+        return X
+
+    def init_cold(self):
+        X = np.zeros(self.shape)
+        lib().or_init_cold(self.ptr, _d(X))
+        return X
+
+    def energy(self, X):
+        E = np.zeros(8)
+        lib().or_energy(self.ptr, _d(self._x(X)), _d(E))
+        return E
+
+    def surrogate(self, X, Xw=None, mask=ALL):
+        X = self._x(X)
+        Xw = X if Xw is None else self._x(Xw)
+        E = np.zeros(8)
+        lib().or_surrogate(self.ptr, _d(X), _d(Xw), mask, _d(E))
+        return E
+
+    def apply(self, X, p, Xw=None, mask=ALL):
+        X = self._x(X)
+        Xw = X if Xw is None else self._x(Xw)
+        p = self._x(p)
+        q = np.zeros(self.shape)
+        lib().or_apply(self.ptr, _d(X), _d(Xw), mask, _d(p), _d(q))
+        return q
+
+    def rhs(self, X, Xw=None, mask=ALL):
+        X = self._x(X)
+        Xw = X if Xw is None else self._x(Xw)
+        g = np.zeros(self.shape)
+        lib().or_rhs(self.ptr, _d(X), _d(Xw), mask, _d(g))
+        return g
+
+    def diag(self, X, Xw=None, mask=ALL):
+        X = self._x(X)
+        Xw = X if Xw is None else self._x(Xw)
+        d = np.zeros(self.shape)
+        lib().or_diag(self.ptr, _d(X), _d(Xw), mask, _d(d))
+        return d
+
+    def residuals(self, X, Xw=None, mask=ALL, with_terms=False):
+        X = self._x(X)
+        Xw = X if Xw is None else self._x(Xw)
+        n = lib().or_residuals(self.ptr, _d(X), _d(Xw), mask, None, None, 0)
+        F = np.zeros(n)
+        t = np.zeros(n, np.int32)
+        lib().or_residuals(self.ptr, _d(X), _d(Xw), mask, _d(F), t.ctypes.data_as(ctypes.POINTER(ctypes.c_int)), n)
+        return (F, t) if with_terms else F
+
+    def pcg(self, X, M):
+        X = self._x(X)
+        delta = np.zeros(self.shape)
+        rz = np.zeros(M + 1)
+        lib().or_pcg(self.ptr, _d(X), int(M), _d(delta), _d(rz))
+        return delta, rz
+
+    def gn_step(self, X, M):
+        X = self._x(X).copy()
+        lib().or_gn_step(self.ptr, _d(X), int(M))
+        return X
+
+    def dense_normal(self, X):
+        A = np.zeros((3, self.K, self.K))
+        g = np.zeros((3, self.K))
+        lib().or_dense_normal(self.ptr, _d(self._x(X)), _d(A), _d(g))
+        return A, g
+
+
+def dense_solve(A, g):
+    """Delta b (K, 3) from the three K x K blocks by SVD pseudo-inverse (Sec. 6.1)."""
+    K = A.shape[1]
+    db = np.zeros((K, 3))
+    for c in range(3):
+        U, s, Vt = np.linalg.svd(A[c])
+        keep = s > s[0] * 1e-14
+        db[:, c] = Vt[keep].T @ ((U[:, keep].T @ g[c]) / s[keep])
+    return db
+
+
+def solve_frame(pb: Problem, X, N: int, M: int, refine: bool = True):
+    """N outer flip-flop iterations (Sec. 6.1): a Gauss-Newton step on the layers
+    (M PCG steps) with the base colours fixed, then the base-colour step with the
+    layers fixed.  Returns the final X, b and the exact energy after each outer
+    iteration (energy history has N + 1 rows, row 0 at the initial state)."""
+    X = _f64(X).copy()
+    hist = [pb.energy(X)]
+    for _ in range(N):
+        X = pb.gn_step(X, M)
+        if refine:
+            A, g = pb.dense_normal(X)
+            pb.set_b(pb.b_init + dense_solve(A, g))
+        hist.append(pb.energy(X))
+    return X, pb.b.copy(), np.array(hist)

@@ -1,0 +1,175 @@
+"""Pins of the oracle's exact energy terms and per-frame precompute (CPU only).
+
+Each test builds a state whose energy the paper's definitions fix in closed form
+by a route other than the oracle's loops (a count of pixels times a per-pixel
+value, a ramp's constant gradient, ...), so a dropped term, wrong sign, wrong
+index or transposed operand in the oracle fails here.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1908_01961_b300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def make_problem(H, W, K, seed=0, I=None, labels=None, b=None, wsr=None, off_s=((1, 2), (-2, 1)), omega=None,
+                 **weights):
+    rng = np.random.default_rng(seed)
+    if labels is None:
+        labels = rng.integers(0, K, size=(H, W)).astype(np.uint8)
+    if b is None:
+        b = rng.uniform(0.2, 0.8, size=(K, 3))
+    if I is None:
+        I = rng.uniform(0.1, 0.9, size=(3, H, W))
+    if wsr is None:
+        wsr = rng.uniform(0, 1, size=(H, W))
+    off_s = np.asarray(off_s, np.int32).reshape(-1, 2)
+    if omega is None:
+        omega = rng.uniform(0, 1, size=(len(off_s), H, W))
+    return O.Problem(I, labels, b, wsr, omega, off_s, **weights)
+
+
+def test_default_parameters_match_paper():
+    g = json.load(open(os.path.join(GOLDEN, "parameters.json")))
+    for k, v in g.items():
+        if k.startswith("_") or k == "pcg_steps_paper":
+            continue
+        assert O.DEFAULT_WEIGHTS[k] == v, k
+
+
+def test_data_residual_zero_at_ground_truth():
+    """eq:data-term vanishes on a noise-free frame built by eq:imageformation."""
+    v = synth.SyntheticVideo(24, 32, 4, 6, seed=3, noise=0.0)
+    f = v.frame(0, noise=False)
+    X = np.concatenate([np.log(f.R), f.T])
+    pb = make_problem(24, 32, 4, I=f.I, labels=f.labels, b=f.b)
+    E = pb.energy(X)
+    assert abs(E[0]) <= 1e-20 * 5000 * 24 * 32 * 3 + 1e-18
+    # and the clustering term then vanishes too, since R = b_label
+    assert abs(E[1]) < 1e-18
+
+
+def test_data_term_closed_form():
+    """Scaling T_0 of a grey-shaded frame by s leaves residual (1-s) I per channel."""
+    H, W, K = 5, 7, 2
+    rng = np.random.default_rng(1)
+    labels = rng.integers(0, K, size=(H, W)).astype(np.uint8)
+    b = rng.uniform(0.2, 0.8, size=(K, 3))
+    R = b[labels].transpose(2, 0, 1)
+    T0 = rng.uniform(0.3, 1.0, size=(H, W))
+    I = R * T0
+    X = np.concatenate([np.log(R), T0[None] * 0.9, np.zeros((K, H, W))])
+    pb = make_problem(H, W, K, I=I, labels=labels, b=b)
+    assert pb.energy(X)[0] == pytest.approx(5000 * np.sum((0.1 * I) ** 2), rel=1e-12)
+
+
+def test_clustering_term_closed_form():
+    H, W, K = 4, 6, 3
+    pb = make_problem(H, W, K)
+    d = np.array([0.1, -0.2, 0.05])
+    X = pb.init_cold()
+    X[:3] += d[:, None, None]
+    assert pb.energy(X)[1] == pytest.approx(200 * H * W * np.sum(d ** 2), rel=1e-12)
+
+
+@pytest.mark.parametrize("p", [1.0, 0.5])
+def test_reflectance_sparsity_ramp(p):
+    """r_c = a_c x + d_c y: interior gradient norm sqrt(|a|^2+|d|^2); the last
+    column keeps only the y part, the last row only the x part, the corner none."""
+    H, W, K = 5, 6, 2
+    a, d = np.array([0.3, -0.1, 0.2]), np.array([-0.05, 0.15, 0.1])
+    pb = make_problem(H, W, K, p=p)
+    X = np.zeros((K + 4, H, W))
+    yy, xx = np.mgrid[0:H, 0:W]
+    for c in range(3):
+        X[c] = a[c] * xx + d[c] * yy
+    A, D = np.linalg.norm(a), np.linalg.norm(d)
+    expect = 20 * ((H - 1) * (W - 1) * np.hypot(A, D) ** p + (H - 1) * D ** p + (W - 1) * A ** p)
+    assert pb.energy(X)[2] == pytest.approx(expect, rel=1e-12)
+
+
+def test_consistency_ramp_and_constant():
+    H, W, K = 6, 7, 2
+    offs = np.array([[1, 2], [-2, 1], [0, -3]], np.int32)
+    pb = make_problem(H, W, K, off_s=offs, omega=np.ones((3, H, W)))
+    X = np.zeros((K + 4, H, W))
+    X[:3] = 0.37
+    assert pb.energy(X)[3] == 0.0
+    slope = 0.2
+    X[:3] = slope * np.mgrid[0:H, 0:W][1]
+    expect = sum(10 * (H - abs(dy)) * (W - abs(dx)) * 3 * (slope * dx) ** 2 for dy, dx in offs)
+    assert pb.energy(X)[3] == pytest.approx(expect, rel=1e-12)
+
+
+def test_monochrome_term():
+    """Grey S (only T_0) gives 0; T_1 = t with b_1 = (1, 0, 0) gives 2 t^2 / 3 per pixel."""
+    H, W, K = 4, 5, 2
+    b = np.array([[1.0, 0.0, 0.0], [0.3, 0.6, 0.2]])
+    pb = make_problem(H, W, K, b=b)
+    X = pb.init_cold()
+    assert abs(pb.energy(X)[4]) < 1e-25
+    t = 0.3
+    X[4] = t
+    assert pb.energy(X)[4] == pytest.approx(10 * pb.wsr.sum() * 2 * t * t / 3, rel=1e-12)
+
+
+def test_isparsity_smoothness_nonneg():
+    H, W, K = 4, 5, 3
+    pb = make_problem(H, W, K)
+    X = pb.init_cold()
+    X[3:] = 0.25
+    E = pb.energy(X)
+    assert E[5] == pytest.approx(3 * K * H * W * 0.25, rel=1e-12)   # T_0 excluded from i-sparsity
+    assert E[6] == 0.0 and E[7] == 0.0                                # constant, non-negative layers
+    s = 0.07
+    X[3:] = -s * np.mgrid[0:H, 0:W][0]                                # ramp down the rows
+    E = pb.energy(X)
+    assert E[6] == pytest.approx(3 * (K + 1) * (H - 1) * W * s, rel=1e-12)
+    assert E[7] == pytest.approx(1000 * (K + 1) * W * s * sum(range(H)), rel=1e-12)
+
+
+def test_precompute_uniform_and_two_colour():
+    """Uniform image: dC = 0, w_SR = 0, pair weights 1 inside and 0 outside.
+    Two-colour split: w_SR = 1 - exp(-50 d) on the two boundary columns only."""
+    H, W = 4, 6
+    col = np.array([0.2, 0.5, 0.3])
+    I = np.broadcast_to(col[:, None, None], (3, H, W)).copy()
+    offs = np.array([[0, 2], [1, -1]], np.int32)
+    C, wsr, om, _ = O.precompute(I, offs)
+    assert np.allclose(C, (col / (col.sum() + 1e-6))[:, None, None], atol=1e-15)
+    assert np.all(wsr == 0)
+    assert np.all(om[0][:, : W - 2] == 1) and np.all(om[0][:, W - 2:] == 0)
+    assert np.all(om[1][: H - 1, 1:] == 1) and np.all(om[1][H - 1] == 0) and np.all(om[1][:, 0] == 0)
+    col2 = np.array([0.6, 0.1, 0.3])
+    I[:, :, 3:] = col2[:, None, None]
+    C, wsr, om, _ = O.precompute(I, offs)
+    d = np.linalg.norm(col / (col.sum() + 1e-6) - col2 / (col2.sum() + 1e-6))
+    expect = np.zeros((H, W))
+    expect[:, 2:4] = 1 - np.exp(-50 * d)
+    assert np.allclose(wsr, expect, atol=1e-15)
+    # pair (x, x + (0, 2)) crosses the split for x = 1, 2
+    assert np.allclose(om[0][:, 1:3], np.exp(-d * d / 0.05 ** 2), rtol=1e-12)
+
+
+def test_temporal_pairs_weight_and_energy():
+    H, W, K = 4, 5, 2
+    rng = np.random.default_rng(5)
+    I = rng.uniform(0.1, 0.9, size=(3, H, W))
+    offs_t = np.array([[0, 0], [1, 1]], np.int32)
+    C, wsr, om_s, om_t = O.precompute(I, np.zeros((0, 2), np.int32), offs_t, Iprev=I)
+    assert np.all(om_t[0] == 1.0)                     # the same pixel, same chromaticity
+    rprev = rng.normal(size=(3, H, W))
+    pb = O.Problem(I, rng.integers(0, K, (H, W)), rng.uniform(0.2, 0.8, (K, 3)), wsr, om_s, np.zeros((0, 2)),
+                   omega_t=om_t, off_t=offs_t, rprev=rprev)
+    X = pb.init_cold()
+    X[:3] = rprev + 0.1                                   # offset 0.1 against the previous frame
+    E = pb.energy(X)[3]
+    # offset (0,0) pairs contribute 10 * 1 * 3 * 0.01 per pixel; offset (1,1) its own
+    e1 = sum(10 * om_t[1][y, x] * np.sum((X[:3, y, x] - rprev[:, y + 1, x + 1]) ** 2)
+             for y in range(H - 1) for x in range(W - 1))
+    assert E == pytest.approx(10 * 3 * 0.01 * H * W + e1, rel=1e-12)
