@@ -1,0 +1,193 @@
+/*
+ * gid.h -- C ABI of the B300 (sm_103a) illumination decomposition solver.
+ *
+ * The library computes, per video frame, the decomposition of Sec. 3
+ * (eq:imageformation)
+ *
+ *     I(x) = R(x) * sum_{k=0..K} b_k T_k(x),   b_0 = (1, 1, 1),
+ *
+ * into reflectance R, direct illumination T_0 and K indirect layers T_1..T_K,
+ * by the alternating sparse-dense solve of Sec. 6.1: a Gauss-Newton step on the
+ * layers (normal equations of eq:optimization solved by M steps of Jacobi-
+ * preconditioned conjugate gradient, IRLS reweighting of Sec. 5.3) with the base
+ * colours fixed, then the base-colour refinement of eq:basecolorrefinement with
+ * the layers fixed.  The energy is eq:giv-energy with the terms of Sec. 5.
+ *
+ * Conventions shared by every call:
+ *   - Every function returns GID_OK (0) or a negative GID_ERR_* code and never
+ *     throws; gid_last_error() gives a message for the last failure.
+ *   - Image buffers are planar, contiguous, float32 (or uint8 for labels):
+ *     channel-major [C][H][W].  Pointers named *_dev are CUDA device pointers,
+ *     *_host are host pointers.  The caller owns every buffer it passes; the
+ *     library copies what it keeps.  The context owns its internal device
+ *     buffers and frees them in gid_destroy().
+ *   - Work is enqueued on the CUDA stream given to gid_create() (0 = legacy
+ *     default stream) and is asynchronous unless a call says it synchronises.
+ *   - There is no CPU fallback: without a usable CUDA device gid_create() fails
+ *     with GID_ERR_CUDA.
+ */
+#ifndef GID_H
+#define GID_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GID_OK 0
+#define GID_ERR_INVALID_ARG (-1) /* bad size, pointer or flag */
+#define GID_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define GID_ERR_OOM (-3)         /* device allocation failed */
+#define GID_ERR_STATE (-4)       /* call out of order, e.g. gid_run before gid_set_frame */
+#define GID_ERR_TIMEOUT (-5)     /* a bounded device wait gave up */
+#define GID_ERR_NUMERIC (-6)     /* non-finite energy/state or a singular base-colour system */
+
+#define GID_MAX_K 10     /* base colours (the paper uses an upper bound of K = 10, Sec. 4.1) */
+#define GID_MAX_PAIRS 8  /* consistency pair offsets per kind (spatial / temporal) */
+
+/* Term weights and solver readings.  Defaults (gid_default_weights) are the
+ * fixed parameter set of Sec. 7 "Parameters": lambda_clustering 200,
+ * lambda_rsparsity 20, p 1, lambda_isparsity 3, lambda_smoothness 3,
+ * lambda_nonneg 1000, lambda_data 5000, lambda_IR 10, lambda_CR 100,
+ * lambda_rconsistency = lambda_monochrome = 10; eps 0.002 (Sec. 5.3.1);
+ * soft-Retinex sharpness 50 (Sec. 5.2). */
+typedef struct {
+  float lambda_data, lambda_clustering, lambda_rsparsity, p, lambda_rconsistency, lambda_monochrome,
+      lambda_isparsity, lambda_smoothness, lambda_nonneg, lambda_IR, lambda_CR, eps, retinex_sharpness;
+  float consistency_tau;  /* soft chromaticity closeness exp(-|dC|^2/tau^2) of the pairs, default 0.05 */
+  int nonneg_strict;      /* 1 (default): non-neg weight is 0 only for T > 0, as printed in Sec. 5.3.1 */
+  int irls_half;          /* 1: halve every IRLS weight (majorise-minimise variant); default 0 */
+  int rcluster_follows_b; /* 1: R_cluster uses the refined base colours; default 0 (initial colours) */
+  int temporal;           /* 1: temporal consistency pairs against the previous solved frame */
+  int refine_base_colors; /* 0 off, 1 after every Gauss-Newton step (default), 2 on the first frame only */
+  int n_spatial_pairs;    /* <= GID_MAX_PAIRS */
+  int n_temporal_pairs;   /* <= GID_MAX_PAIRS */
+  int spatial_offsets[2 * GID_MAX_PAIRS];  /* (dy, dx) per pair, |dy|,|dx| <= 3 */
+  int temporal_offsets[2 * GID_MAX_PAIRS]; /* (dy, dx) per pair into the previous frame, |dy|,|dx| <= 3 */
+} gid_weights;
+
+typedef struct gid_ctx gid_ctx;
+
+/* Fill *w with the defaults above, no pairs and temporal off. */
+void gid_default_weights(gid_weights* w);
+
+/* Create a solver for H x W frames with K base colours (1 <= K <= GID_MAX_K,
+ * H, W >= 1).  Allocates about (8 (K + 4) + 22) planes of H x W floats on the
+ * current device.  stream: a cudaStream_t or NULL.  On success *out owns the
+ * context; on failure *out is NULL and the code says why (GID_ERR_OOM,
+ * GID_ERR_CUDA, GID_ERR_INVALID_ARG). */
+int gid_create(int H, int W, int K, const gid_weights* w, void* stream, gid_ctx** out);
+
+/* Free every device buffer of the context.  NULL is a no-op. */
+void gid_destroy(gid_ctx* ctx);
+
+/* Message of the last failing call on ctx (or of the last failing gid_create
+ * when ctx is NULL).  Valid until the next call on ctx. */
+const char* gid_last_error(const gid_ctx* ctx);
+
+/* Initial base colours b_1..b_K (K x 3 row-major, host): the clustered colours
+ * of Sec. 4.1.  They are the anchor of the refinement (eq:basecolorrefinement)
+ * and the colours of R_cluster.  Also resets the refined colours to them.
+ * Every value must be finite and > 0 (R_cluster uses ln b).  Synchronises. */
+int gid_set_base_colors(gid_ctx* ctx, const float* b_host);
+
+/* Current (refined) base colours b_1..b_K into b_host (K x 3).  Synchronises. */
+int gid_get_base_colors(gid_ctx* ctx, float* b_host);
+
+/* Ingest a frame: rgb_dev is 3 x H x W float32 (the frame I), labels_dev is
+ * H x W uint8 with values 0..K-1, the cluster of each pixel (label k-1 means
+ * base colour b_k).  Computes the chromaticity C = I / (I_R + I_G + I_B + 1e-6)
+ * (Sec. 4.1), the soft-Retinex weight w_SR of Sec. 5.2 and the consistency pair
+ * weights.  If temporal pairs are on and a frame was solved before, that
+ * frame's log reflectance and chromaticity become the previous frame.  Labels
+ * >= K are reported as GID_ERR_INVALID_ARG by the next synchronising call. */
+int gid_set_frame(gid_ctx* ctx, const float* rgb_dev, const uint8_t* labels_dev);
+
+/* Initial state: mode 0 = cold start (r = ln R_cluster, T_0 = mean_c I /
+ * mean_c R_cluster, T_k = 0), mode 1 = warm start (keep the previous frame's
+ * layers and base colours; needs a solved frame).  Requires gid_set_frame. */
+int gid_init(gid_ctx* ctx, int mode);
+
+/* Run n_outer flip-flop iterations (Sec. 6.1): each a Gauss-Newton step of
+ * exactly m_inner PCG steps on the layers, then (per refine_base_colors) the
+ * base-colour step.  Asynchronous.  n_outer >= 0, m_inner >= 1. */
+int gid_run(gid_ctx* ctx, int n_outer, int m_inner);
+
+/* Layers of the current state: R_dev (3 x H x W) = exp(r), T_dev ((K+1) x H x W)
+ * = T_0..T_K.  Either pointer may be NULL.  Asynchronous. */
+int gid_get_layers(gid_ctx* ctx, float* R_dev, float* T_dev);
+
+/* Raw unknowns X ((K+4) x H x W: r_R, r_G, r_B, T_0..T_K, r = ln R) to / from
+ * device memory.  gid_set_state also marks the context initialised.  Async. */
+int gid_get_state(gid_ctx* ctx, float* X_dev);
+int gid_set_state(gid_ctx* ctx, const float* X_dev);
+
+/* Exact energy of the current state (eq:giv-energy; the l1, l_p and max terms
+ * exactly, not their IRLS surrogates): per_term[8] in the order data,
+ * clustering, r-sparsity, r-consistency, monochrome, i-sparsity, smoothness,
+ * non-neg; *total their sum (FP64 reductions).  Either pointer may be NULL.
+ * Synchronises; returns GID_ERR_NUMERIC if the state is not finite, and any
+ * error a device step recorded since the last synchronising call. */
+int gid_energy(gid_ctx* ctx, double* total, double* per_term);
+
+/* One whole frame with host buffers: copy rgb_host (3 x H x W) and labels_host
+ * (H x W) to the device, gid_set_frame, gid_init(init_mode), gid_run(n_outer,
+ * m_inner), copy R (3 x H x W), T ((K+1) x H x W) and the refined base colours
+ * (K x 3) back.  Output pointers may be NULL.  Staging buffers are allocated on
+ * the first call.  Synchronises. */
+int gid_solve_frame_host(gid_ctx* ctx, const float* rgb_host, const uint8_t* labels_host, int init_mode,
+                         int n_outer, int m_inner, float* R_host, float* T_host, float* b_host);
+
+/* ---- single stages, for kernel-level checks (same kernels as gid_run) ---- */
+
+/* Per-frame precompute outputs: w_SR (H x W), spatial pair weights
+ * (n_spatial x H x W) and temporal pair weights (n_temporal x H x W; zeros if
+ * the temporal pairs are inactive for this frame).  NULL pointers skip. Async. */
+int gid_stage_precompute(gid_ctx* ctx, float* wsr_dev, float* omega_s_dev, float* omega_t_dev);
+
+/* Normal equations at the current state X: g_dev = -J^T F and diag_dev =
+ * diag(J^T J), each (K+4) x H x W.  Does not change X.  Async. */
+int gid_stage_linearize(gid_ctx* ctx, float* g_dev, float* diag_dev);
+
+/* q_dev = J^T J p_dev at the current state (both (K+4) x H x W).  Async. */
+int gid_stage_apply(gid_ctx* ctx, const float* p_dev, float* q_dev);
+
+/* delta_dev = the Gauss-Newton update after exactly m_inner PCG steps at the
+ * current state, without applying it.  Async. */
+int gid_stage_pcg(gid_ctx* ctx, int m_inner, float* delta_dev);
+
+/* Base-colour normal equations at the current state: A_host (3 x K x K) and
+ * g_host (3 x K), one K x K block per channel (eq:basecolorrefinement).
+ * Synchronises. */
+int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
+
+/* ---- instrumentation ---- */
+
+/* Kernel kinds for gid_profile_read. */
+#define GID_KIND_FRAME 0     /* frame ingest + prior weights */
+#define GID_KIND_INIT 1      /* cold start */
+#define GID_KIND_LINEARIZE 2 /* fused residual / Jacobian / preconditioner / PCG start */
+#define GID_KIND_APPLY 3     /* PCG operator step q = J^T J p */
+#define GID_KIND_UPDATE 4    /* PCG vector step */
+#define GID_KIND_DENSE 5     /* base-colour normal equations + solve */
+#define GID_KIND_ENERGY 6
+#define GID_KIND_READOUT 7
+#define GID_NUM_KINDS 8
+
+/* Number of kernels this context has launched since gid_create. */
+int gid_launch_count(const gid_ctx* ctx, long long* n);
+
+/* enable != 0: bracket every later kernel launch with CUDA events on the
+ * context stream (up to 8192 launches between reads); 0 stops recording. */
+int gid_profile(gid_ctx* ctx, int enable);
+
+/* Synchronise and return, per kind, the summed device time (ms[GID_NUM_KINDS])
+ * and launch count (count[GID_NUM_KINDS]) recorded since the previous read. */
+int gid_profile_read(gid_ctx* ctx, double* ms, long long* count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GID_H */

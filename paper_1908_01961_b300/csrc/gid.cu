@@ -1,0 +1,606 @@
+// C ABI of the illumination decomposition solver: context, buffers, launch
+// sequence.  See include/gid.h for the contract of every entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/gid.h"
+#include "gid_kernels.cuh"
+
+using namespace gid;
+
+struct gid_ctx {
+  int H = 0, W = 0, K = 0, V = 0, pitch = 0;
+  long plane = 0;
+  gid_weights w{};
+  cudaStream_t stream = nullptr;
+  char* pool = nullptr;
+  size_t pool_bytes = 0;
+  float *I = nullptr, *C = nullptr, *Cprev = nullptr, *rprev = nullptr, *wsr = nullptr, *ws = nullptr, *wt = nullptr,
+        *wtsum = nullptr;
+  uint8_t* lab = nullptr;
+  float *X = nullptr, *d = nullptr, *r = nullptr, *z = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr,
+        *Minv = nullptr;
+  DevColors* col = nullptr;
+  DevScalars* sc = nullptr;
+  double* partial = nullptr;
+  // staging for the host-buffer entry point (allocated on first use)
+  float* st_rgb = nullptr;
+  uint8_t* st_lab = nullptr;
+  float *st_R = nullptr, *st_T = nullptr;
+  bool has_colors = false, has_frame = false, initialised = false, temporal_active = false;
+  int frames_solved = 0;
+  long long launches = 0;  // kernels launched by this context
+  // optional per-kernel CUDA-event timing (gid_profile)
+  bool prof = false;
+  std::vector<cudaEvent_t> ev;
+  std::vector<int> ev_kind;  // kind of each (start, end) pair
+  double prof_ms[GID_NUM_KINDS] = {0};
+  long long prof_n[GID_NUM_KINDS] = {0};
+  std::string err;
+};
+
+static std::string g_create_err;
+
+#define GID_TRY_CUDA(ctx, call)                                                             \
+  do {                                                                                      \
+    cudaError_t e_ = (call);                                                                \
+    if (e_ != cudaSuccess) return fail((ctx), GID_ERR_CUDA, #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+static int fail(gid_ctx* ctx, int code, const char* what, const char* detail = nullptr) {
+  std::string m = what;
+  if (detail) m += std::string(": ") + detail;
+  if (ctx)
+    ctx->err = m;
+  else
+    g_create_err = m;
+  return code;
+}
+
+// Wraps one kernel launch: counts it and, when profiling, brackets it with events.
+template <class F>
+static void launch(gid_ctx* c, int kind, F f) {
+  const size_t i = c->ev_kind.size();
+  if (c->prof && 2 * i + 1 < c->ev.size()) {
+    cudaEventRecord(c->ev[2 * i], c->stream);
+    f();
+    cudaEventRecord(c->ev[2 * i + 1], c->stream);
+    c->ev_kind.push_back(kind);
+  } else {
+    f();
+  }
+  c->launches++;
+}
+
+static Weights to_dev(const gid_weights& w) {
+  Weights d;
+  d.ld = w.lambda_data;
+  d.lcl = w.lambda_clustering;
+  d.lrs = w.lambda_rsparsity;
+  d.p = w.p;
+  d.lrc = w.lambda_rconsistency;
+  d.lm = w.lambda_monochrome;
+  d.lis = w.lambda_isparsity;
+  d.lsm = w.lambda_smoothness;
+  d.lnn = w.lambda_nonneg;
+  d.lIR = w.lambda_IR;
+  d.lCR = w.lambda_CR;
+  d.eps = w.eps;
+  d.sharp = w.retinex_sharpness;
+  d.tau = w.consistency_tau;
+  d.nonneg_strict = w.nonneg_strict;
+  d.irls_half = w.irls_half;
+  d.rcluster_follows_b = w.rcluster_follows_b;
+  return d;
+}
+
+static Params params(const gid_ctx* c) {
+  Params P;
+  memset(&P, 0, sizeof(P));
+  P.H = c->H;
+  P.W = c->W;
+  P.pitch = c->pitch;
+  P.plane = c->plane;
+  P.w = to_dev(c->w);
+  P.I = c->I;
+  P.lab = c->lab;
+  P.wsr = c->wsr;
+  P.ws = c->ws;
+  P.wt = c->wt;
+  P.wtsum = c->wtsum;
+  P.rprev = c->rprev;
+  P.ns = c->w.n_spatial_pairs;
+  P.nt = c->w.n_temporal_pairs;
+  P.temporal = c->temporal_active ? 1 : 0;
+  for (int i = 0; i < 2 * GID_MAX_PAIRS; i++) {
+    P.off_s[i] = c->w.spatial_offsets[i];
+    P.off_t[i] = c->w.temporal_offsets[i];
+  }
+  P.X = c->X;
+  P.d = c->d;
+  P.r = c->r;
+  P.z = c->z;
+  P.q = c->q;
+  P.Minv = c->Minv;
+  P.col = c->col;
+  P.sc = c->sc;
+  P.partial = c->partial;
+  return P;
+}
+
+static dim3 pix_grid(const gid_ctx* c) { return dim3((c->W + BX - 1) / BX, (c->H + BY - 1) / BY); }
+static int dense_blocks(const gid_ctx* c) {
+  long P = (long)c->H * c->W;
+  long nb = (P + 256 * 8 - 1) / (256 * 8);
+  return (int)std::max(1L, std::min(nb, 296L));
+}
+
+// ---------------------------------------------------------------- K dispatch
+
+template <int K>
+struct Launch {
+  static void linearize(const gid_ctx* c, int mode, float* g, float* dg) {
+    k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg);
+  }
+  static void apply(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
+    k_apply<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, first, pin, pout, qout);
+  }
+  static void update(const gid_ctx* c, const float* p, int last) {
+    k_update<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), p, last);
+  }
+  static void dense(const gid_ctx* c, int solve) {
+    k_dense<K><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
+  }
+  static void energy(const gid_ctx* c) { k_energy<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
+  static void init_cold(const gid_ctx* c) { k_init_cold<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
+  static void readout(const gid_ctx* c, float* R, float* T) {
+    k_readout<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), R, T);
+  }
+};
+
+#define GID_DISPATCH(ctx, fn, ...)               \
+  switch ((ctx)->K) {                            \
+    case 1: Launch<1>::fn(__VA_ARGS__); break;   \
+    case 2: Launch<2>::fn(__VA_ARGS__); break;   \
+    case 3: Launch<3>::fn(__VA_ARGS__); break;   \
+    case 4: Launch<4>::fn(__VA_ARGS__); break;   \
+    case 5: Launch<5>::fn(__VA_ARGS__); break;   \
+    case 6: Launch<6>::fn(__VA_ARGS__); break;   \
+    case 7: Launch<7>::fn(__VA_ARGS__); break;   \
+    case 8: Launch<8>::fn(__VA_ARGS__); break;   \
+    case 9: Launch<9>::fn(__VA_ARGS__); break;   \
+    case 10: Launch<10>::fn(__VA_ARGS__); break; \
+    default: break;                              \
+  }
+
+static int check_launch(gid_ctx* c, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, what, cudaGetErrorString(e));
+  return GID_OK;
+}
+
+// Reads and clears the device status word; synchronises the stream.
+static int sync_status(gid_ctx* c) {
+  int st = 0;
+  GID_TRY_CUDA(c, cudaMemcpyAsync(&st, &c->sc->status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  if (st) {
+    int zero = 0;
+    GID_TRY_CUDA(c, cudaMemcpyAsync(&c->sc->status, &zero, sizeof(int), cudaMemcpyHostToDevice, c->stream));
+    GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (st & ST_BAD_LABEL) return fail(c, GID_ERR_INVALID_ARG, "a label was >= K (treated as 0)");
+    if (st & ST_SINGULAR) return fail(c, GID_ERR_NUMERIC, "base-colour normal equations not positive definite");
+  }
+  return GID_OK;
+}
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" void gid_default_weights(gid_weights* w) {
+  if (!w) return;
+  memset(w, 0, sizeof(*w));
+  w->lambda_data = 5000.f;
+  w->lambda_clustering = 200.f;
+  w->lambda_rsparsity = 20.f;
+  w->p = 1.f;
+  w->lambda_rconsistency = 10.f;
+  w->lambda_monochrome = 10.f;
+  w->lambda_isparsity = 3.f;
+  w->lambda_smoothness = 3.f;
+  w->lambda_nonneg = 1000.f;
+  w->lambda_IR = 10.f;
+  w->lambda_CR = 100.f;
+  w->eps = 0.002f;
+  w->retinex_sharpness = 50.f;
+  w->consistency_tau = 0.05f;
+  w->nonneg_strict = 1;
+  w->irls_half = 0;
+  w->rcluster_follows_b = 0;
+  w->temporal = 0;
+  w->refine_base_colors = 1;
+}
+
+static bool weights_ok(const gid_weights* w) {
+  if (w->n_spatial_pairs < 0 || w->n_spatial_pairs > GID_MAX_PAIRS) return false;
+  if (w->n_temporal_pairs < 0 || w->n_temporal_pairs > GID_MAX_PAIRS) return false;
+  for (int i = 0; i < 2 * w->n_spatial_pairs; i++)
+    if (std::abs(w->spatial_offsets[i]) > 3) return false;
+  for (int i = 0; i < 2 * w->n_temporal_pairs; i++)
+    if (std::abs(w->temporal_offsets[i]) > 3) return false;
+  if (!(w->eps > 0.f) || !(w->consistency_tau > 0.f)) return false;
+  if (w->refine_base_colors < 0 || w->refine_base_colors > 2) return false;
+  return true;
+}
+
+extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* stream, gid_ctx** out) {
+  if (!out) return fail(nullptr, GID_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (H < 1 || W < 1 || K < 1 || K > GID_MAX_K) return fail(nullptr, GID_ERR_INVALID_ARG, "bad H, W or K");
+  if ((long)H * W > (1L << 28)) return fail(nullptr, GID_ERR_INVALID_ARG, "frame too large");
+  gid_weights def;
+  gid_default_weights(&def);
+  if (!w) w = &def;
+  if (!weights_ok(w)) return fail(nullptr, GID_ERR_INVALID_ARG, "bad weights (pairs, offsets, eps, tau or flags)");
+  int dev_count = 0;
+  cudaError_t e = cudaGetDeviceCount(&dev_count);
+  if (e != cudaSuccess || dev_count < 1)
+    return fail(nullptr, GID_ERR_CUDA, "no CUDA device", e != cudaSuccess ? cudaGetErrorString(e) : nullptr);
+  gid_ctx* c = new (std::nothrow) gid_ctx();
+  if (!c) return fail(nullptr, GID_ERR_OOM, "host allocation");
+  c->H = H;
+  c->W = W;
+  c->K = K;
+  c->V = K + 4;
+  c->w = *w;
+  c->stream = (cudaStream_t)stream;
+  c->pitch = (W + 31) / 32 * 32;
+  c->plane = (long)H * c->pitch;
+  const int ns = std::max(1, w->n_spatial_pairs), nt = std::max(1, w->n_temporal_pairs);
+  // planes: I 3, C 3, Cprev 3, rprev 3, wsr 1, ws ns, wt nt, wtsum 1, X d r z pA pB q Minv 8V
+  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V;
+  const size_t fbytes = (size_t)nplanes * c->plane * sizeof(float) + 256 * (size_t)nplanes;
+  const size_t lbytes = ((size_t)c->plane + 255) / 256 * 256;
+  const long nb = (long)pix_grid(c).x * pix_grid(c).y;
+  const long npart = std::max(nb * 8, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K));
+  const size_t pbytes = (size_t)npart * sizeof(double);
+  c->pool_bytes = fbytes + lbytes + 256 * 8 + sizeof(DevColors) + sizeof(DevScalars) + pbytes;
+  e = cudaMalloc(&c->pool, c->pool_bytes);
+  if (e != cudaSuccess) {
+    delete c;
+    return fail(nullptr, GID_ERR_OOM, "cudaMalloc", cudaGetErrorString(e));
+  }
+  char* p = c->pool;
+  auto take = [&](size_t bytes) {
+    char* r = p;
+    p += (bytes + 255) / 256 * 256;
+    return r;
+  };
+  auto planes = [&](long n) { return (float*)take((size_t)n * c->plane * sizeof(float)); };
+  c->I = planes(3);
+  c->C = planes(3);
+  c->Cprev = planes(3);
+  c->rprev = planes(3);
+  c->wsr = planes(1);
+  c->ws = planes(ns);
+  c->wt = planes(nt);
+  c->wtsum = planes(1);
+  c->X = planes(c->V);
+  c->d = planes(c->V);
+  c->r = planes(c->V);
+  c->z = planes(c->V);
+  c->pA = planes(c->V);
+  c->pB = planes(c->V);
+  c->q = planes(c->V);
+  c->Minv = planes(c->V);
+  c->lab = (uint8_t*)take(lbytes);
+  c->col = (DevColors*)take(sizeof(DevColors));
+  c->sc = (DevScalars*)take(sizeof(DevScalars));
+  c->partial = (double*)take(pbytes);
+  if ((size_t)(p - c->pool) > c->pool_bytes) {
+    cudaFree(c->pool);
+    delete c;
+    return fail(nullptr, GID_ERR_OOM, "internal pool layout");
+  }
+  e = cudaMemsetAsync(c->pool, 0, c->pool_bytes, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    cudaFree(c->pool);
+    delete c;
+    return fail(nullptr, GID_ERR_CUDA, "cudaMemset", cudaGetErrorString(e));
+  }
+  *out = c;
+  return GID_OK;
+}
+
+extern "C" void gid_destroy(gid_ctx* c) {
+  if (!c) return;
+  if (c->stream)
+    cudaStreamSynchronize(c->stream);
+  else
+    cudaDeviceSynchronize();
+  for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  cudaFree(c->pool);
+  cudaFree(c->st_rgb);
+  cudaFree(c->st_lab);
+  cudaFree(c->st_R);
+  cudaFree(c->st_T);
+  delete c;
+}
+
+extern "C" const char* gid_last_error(const gid_ctx* c) { return c ? c->err.c_str() : g_create_err.c_str(); }
+
+extern "C" int gid_set_base_colors(gid_ctx* c, const float* b_host) {
+  if (!c || !b_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  DevColors h;
+  memset(&h, 0, sizeof(h));
+  for (int i = 0; i < c->K * 3; i++) {
+    if (!std::isfinite(b_host[i]) || !(b_host[i] > 0.f))
+      return fail(c, GID_ERR_INVALID_ARG, "base colours must be finite and > 0");
+    h.b[i] = h.binit[i] = b_host[i];
+    h.bd[i] = b_host[i];
+  }
+  GID_TRY_CUDA(c, cudaMemcpyAsync(c->col, &h, sizeof(h), cudaMemcpyHostToDevice, c->stream));
+  GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  c->has_colors = true;
+  return GID_OK;
+}
+
+extern "C" int gid_get_base_colors(gid_ctx* c, float* b_host) {
+  if (!c || !b_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  DevColors h;
+  GID_TRY_CUDA(c, cudaMemcpyAsync(&h, c->col, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+  int rc = sync_status(c);
+  for (int i = 0; i < c->K * 3; i++) b_host[i] = h.b[i];
+  return rc;
+}
+
+extern "C" int gid_set_frame(gid_ctx* c, const float* rgb_dev, const uint8_t* labels_dev) {
+  if (!c || !rgb_dev || !labels_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  const bool temporal = c->w.temporal && c->w.n_temporal_pairs > 0 && c->frames_solved > 0;
+  if (temporal) {
+    // The solved frame becomes the previous frame: its r and its chromaticity.
+    GID_TRY_CUDA(c, cudaMemcpyAsync(c->rprev, c->X, sizeof(float) * 3 * c->plane, cudaMemcpyDeviceToDevice,
+                                    c->stream));
+    std::swap(c->C, c->Cprev);
+  }
+  c->temporal_active = temporal;
+  Params P = params(c);
+  launch(c, GID_KIND_FRAME, [&] {
+    k_ingest<<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(P, rgb_dev, labels_dev, c->K, c->C, c->lab, c->I);
+  });
+  if (int rc = check_launch(c, "k_ingest")) return rc;
+  launch(c, GID_KIND_FRAME, [&] {
+    k_prior_weights<<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(P, c->C, c->Cprev, c->wsr, c->ws, c->wt,
+                                                                  c->wtsum);
+  });
+  if (int rc = check_launch(c, "k_prior_weights")) return rc;
+  c->has_frame = true;
+  return GID_OK;
+}
+
+extern "C" int gid_init(gid_ctx* c, int mode) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (!c->has_frame || !c->has_colors)
+    return fail(c, GID_ERR_STATE, "gid_init needs gid_set_base_colors and gid_set_frame");
+  if (mode == 0) {
+    launch(c, GID_KIND_INIT, [&] { GID_DISPATCH(c, init_cold, c); });
+    if (int rc = check_launch(c, "k_init_cold")) return rc;
+  } else if (mode == 1) {
+    if (!c->initialised) return fail(c, GID_ERR_STATE, "warm start needs a previous state");
+  } else {
+    return fail(c, GID_ERR_INVALID_ARG, "init mode must be 0 (cold) or 1 (warm)");
+  }
+  c->initialised = true;
+  return GID_OK;
+}
+
+static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
+  launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
+  if (int rc = check_launch(c, "k_linearize")) return rc;
+  float* pin = c->pB;
+  float* pout = c->pA;
+  for (int m = 1; m <= m_inner; m++) {
+    launch(c, GID_KIND_APPLY, [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, (const float*)pin, pout, c->q); });
+    launch(c, GID_KIND_UPDATE,
+           [&] { GID_DISPATCH(c, update, c, (const float*)pout, m == m_inner ? last_mode : 0); });
+    std::swap(pin, pout);
+  }
+  return check_launch(c, "pcg");
+}
+
+extern "C" int gid_run(gid_ctx* c, int n_outer, int m_inner) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (n_outer < 0 || m_inner < 1) return fail(c, GID_ERR_INVALID_ARG, "n_outer >= 0 and m_inner >= 1");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "gid_run before gid_set_frame / gid_init");
+  const bool refine = c->w.refine_base_colors == 1 || (c->w.refine_base_colors == 2 && c->frames_solved == 0);
+  for (int n = 0; n < n_outer; n++) {
+    if (int rc = enqueue_gn_step(c, m_inner, 1)) return rc;
+    if (refine) {
+      launch(c, GID_KIND_DENSE, [&] { GID_DISPATCH(c, dense, c, 1); });
+      if (int rc = check_launch(c, "k_dense")) return rc;
+    }
+  }
+  c->frames_solved++;
+  return GID_OK;
+}
+
+extern "C" int gid_get_layers(gid_ctx* c, float* R_dev, float* T_dev) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (!c->initialised) return fail(c, GID_ERR_STATE, "no state");
+  if (!R_dev && !T_dev) return GID_OK;
+  launch(c, GID_KIND_READOUT, [&] { GID_DISPATCH(c, readout, c, R_dev, T_dev); });
+  return check_launch(c, "k_readout");
+}
+
+extern "C" int gid_get_state(gid_ctx* c, float* X_dev) {
+  if (!c || !X_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  GID_TRY_CUDA(c, cudaMemcpy2DAsync(X_dev, sizeof(float) * c->W, c->X, sizeof(float) * c->pitch, sizeof(float) * c->W,
+                                    (size_t)c->V * c->H, cudaMemcpyDeviceToDevice, c->stream));
+  return GID_OK;
+}
+
+extern "C" int gid_set_state(gid_ctx* c, const float* X_dev) {
+  if (!c || !X_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  GID_TRY_CUDA(c, cudaMemcpy2DAsync(c->X, sizeof(float) * c->pitch, X_dev, sizeof(float) * c->W, sizeof(float) * c->W,
+                                    (size_t)c->V * c->H, cudaMemcpyDeviceToDevice, c->stream));
+  c->initialised = true;
+  return GID_OK;
+}
+
+extern "C" int gid_energy(gid_ctx* c, double* total, double* per_term) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
+  launch(c, GID_KIND_ENERGY, [&] { GID_DISPATCH(c, energy, c); });
+  if (int rc = check_launch(c, "k_energy")) return rc;
+  double E[8];
+  GID_TRY_CUDA(c, cudaMemcpyAsync(E, c->sc->energy, sizeof(E), cudaMemcpyDeviceToHost, c->stream));
+  int rc = sync_status(c);
+  double t = 0;
+  for (int i = 0; i < 8; i++) t += E[i];
+  if (per_term) memcpy(per_term, E, sizeof(E));
+  if (total) *total = t;
+  if (rc) return rc;
+  if (!std::isfinite(t)) return fail(c, GID_ERR_NUMERIC, "energy is not finite");
+  return GID_OK;
+}
+
+extern "C" int gid_solve_frame_host(gid_ctx* c, const float* rgb_host, const uint8_t* labels_host, int init_mode,
+                                    int n_outer, int m_inner, float* R_host, float* T_host, float* b_host) {
+  if (!c || !rgb_host || !labels_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  const size_t HW = (size_t)c->H * c->W;
+  if (!c->st_rgb) {
+    GID_TRY_CUDA(c, cudaMalloc(&c->st_rgb, 3 * HW * sizeof(float)));
+    GID_TRY_CUDA(c, cudaMalloc(&c->st_lab, HW));
+    GID_TRY_CUDA(c, cudaMalloc(&c->st_R, 3 * HW * sizeof(float)));
+    GID_TRY_CUDA(c, cudaMalloc(&c->st_T, (size_t)(c->K + 1) * HW * sizeof(float)));
+  }
+  GID_TRY_CUDA(c, cudaMemcpyAsync(c->st_rgb, rgb_host, 3 * HW * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+  GID_TRY_CUDA(c, cudaMemcpyAsync(c->st_lab, labels_host, HW, cudaMemcpyHostToDevice, c->stream));
+  if (int rc = gid_set_frame(c, c->st_rgb, c->st_lab)) return rc;
+  if (int rc = gid_init(c, init_mode)) return rc;
+  if (int rc = gid_run(c, n_outer, m_inner)) return rc;
+  if (R_host || T_host) {
+    if (int rc = gid_get_layers(c, c->st_R, c->st_T)) return rc;
+    if (R_host)
+      GID_TRY_CUDA(c, cudaMemcpyAsync(R_host, c->st_R, 3 * HW * sizeof(float), cudaMemcpyDeviceToHost, c->stream));
+    if (T_host)
+      GID_TRY_CUDA(c, cudaMemcpyAsync(T_host, c->st_T, (size_t)(c->K + 1) * HW * sizeof(float),
+                                      cudaMemcpyDeviceToHost, c->stream));
+  }
+  if (b_host) return gid_get_base_colors(c, b_host);
+  return sync_status(c);
+}
+
+// ---------------------------------------------------------------- stages
+
+extern "C" int gid_stage_precompute(gid_ctx* c, float* wsr_dev, float* omega_s_dev, float* omega_t_dev) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (!c->has_frame) return fail(c, GID_ERR_STATE, "no frame");
+  auto out = [&](float* dst, const float* src, int n) -> int {
+    if (!dst || n <= 0) return GID_OK;
+    GID_TRY_CUDA(c, cudaMemcpy2DAsync(dst, sizeof(float) * c->W, src, sizeof(float) * c->pitch, sizeof(float) * c->W,
+                                      (size_t)n * c->H, cudaMemcpyDeviceToDevice, c->stream));
+    return GID_OK;
+  };
+  if (int rc = out(wsr_dev, c->wsr, 1)) return rc;
+  if (int rc = out(omega_s_dev, c->ws, c->w.n_spatial_pairs)) return rc;
+  if (omega_t_dev && c->w.n_temporal_pairs > 0) {
+    if (c->temporal_active) return out(omega_t_dev, c->wt, c->w.n_temporal_pairs);
+    GID_TRY_CUDA(c, cudaMemsetAsync(omega_t_dev, 0, sizeof(float) * c->w.n_temporal_pairs * c->H * c->W, c->stream));
+  }
+  return GID_OK;
+}
+
+// The stage calls reuse the PCG buffers (pA, pB, d) as scratch and copy into /
+// out of the caller's contiguous arrays.
+static int to_pitched(gid_ctx* c, float* dst, const float* src) {
+  GID_TRY_CUDA(c, cudaMemcpy2DAsync(dst, sizeof(float) * c->pitch, src, sizeof(float) * c->W, sizeof(float) * c->W,
+                                    (size_t)c->V * c->H, cudaMemcpyDeviceToDevice, c->stream));
+  return GID_OK;
+}
+static int from_pitched(gid_ctx* c, float* dst, const float* src) {
+  GID_TRY_CUDA(c, cudaMemcpy2DAsync(dst, sizeof(float) * c->W, src, sizeof(float) * c->pitch, sizeof(float) * c->W,
+                                    (size_t)c->V * c->H, cudaMemcpyDeviceToDevice, c->stream));
+  return GID_OK;
+}
+
+extern "C" int gid_stage_linearize(gid_ctx* c, float* g_dev, float* diag_dev) {
+  if (!c || !g_dev || !diag_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
+  launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 1, c->pA, c->pB); });
+  if (int rc = check_launch(c, "k_linearize")) return rc;
+  if (int rc = from_pitched(c, g_dev, c->pA)) return rc;
+  return from_pitched(c, diag_dev, c->pB);
+}
+
+extern "C" int gid_stage_apply(gid_ctx* c, const float* p_dev, float* q_dev) {
+  if (!c || !p_dev || !q_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
+  if (int rc = to_pitched(c, c->pA, p_dev)) return rc;
+  launch(c, GID_KIND_APPLY,
+         [&] { GID_DISPATCH(c, apply, c, 1, 0, (const float*)c->pA, (float*)nullptr, c->pB); });
+  if (int rc = check_launch(c, "k_apply")) return rc;
+  return from_pitched(c, q_dev, c->pB);
+}
+
+extern "C" int gid_stage_pcg(gid_ctx* c, int m_inner, float* delta_dev) {
+  if (!c || !delta_dev || m_inner < 1) return fail(c, GID_ERR_INVALID_ARG, "bad argument");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
+  if (int rc = enqueue_gn_step(c, m_inner, 2)) return rc;
+  return from_pitched(c, delta_dev, c->d);
+}
+
+extern "C" int gid_stage_dense_normal(gid_ctx* c, double* A_host, double* g_host) {
+  if (!c || !A_host || !g_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
+  launch(c, GID_KIND_DENSE, [&] { GID_DISPATCH(c, dense, c, 0); });
+  if (int rc = check_launch(c, "k_dense")) return rc;
+  GID_TRY_CUDA(c, cudaMemcpyAsync(A_host, c->sc->A, sizeof(double) * 3 * c->K * c->K, cudaMemcpyDeviceToHost,
+                                  c->stream));
+  GID_TRY_CUDA(c, cudaMemcpyAsync(g_host, c->sc->g, sizeof(double) * 3 * c->K, cudaMemcpyDeviceToHost, c->stream));
+  return sync_status(c);
+}
+
+// ---------------------------------------------------------------- counters
+
+extern "C" int gid_launch_count(const gid_ctx* c, long long* n) {
+  if (!c || !n) return GID_ERR_INVALID_ARG;
+  *n = c->launches;
+  return GID_OK;
+}
+
+extern "C" int gid_profile(gid_ctx* c, int enable) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (enable && c->ev.empty()) {
+    c->ev.resize(2 * 8192);
+    for (auto& e : c->ev) GID_TRY_CUDA(c, cudaEventCreate(&e));
+  }
+  c->prof = enable != 0;
+  return GID_OK;
+}
+
+extern "C" int gid_profile_read(gid_ctx* c, double* ms, long long* count) {
+  if (!c || !ms || !count) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i < c->ev_kind.size(); i++) {
+    float t = 0.f;
+    GID_TRY_CUDA(c, cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]));
+    c->prof_ms[c->ev_kind[i]] += t;
+    c->prof_n[c->ev_kind[i]]++;
+  }
+  c->ev_kind.clear();
+  for (int k = 0; k < GID_NUM_KINDS; k++) {
+    ms[k] = c->prof_ms[k];
+    count[k] = c->prof_n[k];
+    c->prof_ms[k] = 0;
+    c->prof_n[k] = 0;
+  }
+  return GID_OK;
+}

@@ -1,0 +1,260 @@
+"""Python binding of the C ABI in include/gid.h (argument marshalling only).
+
+Every step of the solve runs in the CUDA library ``libgid.so`` built in-tree by
+``paper_1908_01961_b300.build``; there is no Python or CPU fallback.  PyTorch is
+used only for device memory (tensors whose ``data_ptr()`` is passed through) and
+for the CUDA stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgid.so")
+
+GID_OK = 0
+ERRORS = {-1: "GID_ERR_INVALID_ARG", -2: "GID_ERR_CUDA", -3: "GID_ERR_OOM", -4: "GID_ERR_STATE",
+          -5: "GID_ERR_TIMEOUT", -6: "GID_ERR_NUMERIC"}
+MAX_K = 10
+MAX_PAIRS = 8
+TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness", "non_neg")
+KINDS = ("frame", "init", "linearize", "apply", "update", "dense", "energy", "readout")
+
+# Every function include/gid.h declares.
+EXPORTS = (
+    "gid_default_weights", "gid_create", "gid_destroy", "gid_last_error", "gid_set_base_colors",
+    "gid_get_base_colors", "gid_set_frame", "gid_init", "gid_run", "gid_get_layers", "gid_get_state",
+    "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
+    "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
+    "gid_profile_read",
+)
+
+
+class GidError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{ERRORS.get(code, code)}: {msg}")
+        self.code = code
+
+
+class Weights(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_float) for n in (
+        "lambda_data", "lambda_clustering", "lambda_rsparsity", "p", "lambda_rconsistency", "lambda_monochrome",
+        "lambda_isparsity", "lambda_smoothness", "lambda_nonneg", "lambda_IR", "lambda_CR", "eps",
+        "retinex_sharpness", "consistency_tau")] + [(n, ctypes.c_int) for n in (
+            "nonneg_strict", "irls_half", "rcluster_follows_b", "temporal", "refine_base_colors",
+            "n_spatial_pairs", "n_temporal_pairs")] + [
+        ("spatial_offsets", ctypes.c_int * (2 * MAX_PAIRS)),
+        ("temporal_offsets", ctypes.c_int * (2 * MAX_PAIRS)),
+    ]
+
+
+_lib = None
+
+
+def load():
+    """Load libgid.so (raises if it has not been built: no fallback exists)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1908_01961_b300.build`")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, F = ctypes.c_void_p, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)
+    LL = ctypes.POINTER(ctypes.c_longlong)
+    L.gid_default_weights.argtypes = [ctypes.POINTER(Weights)]
+    L.gid_default_weights.restype = None
+    L.gid_create.argtypes = [I, I, I, ctypes.POINTER(Weights), P, ctypes.POINTER(P)]
+    L.gid_destroy.argtypes = [P]
+    L.gid_destroy.restype = None
+    L.gid_last_error.argtypes = [P]
+    L.gid_last_error.restype = ctypes.c_char_p
+    L.gid_set_base_colors.argtypes = [P, F]
+    L.gid_get_base_colors.argtypes = [P, F]
+    L.gid_set_frame.argtypes = [P, P, P]
+    L.gid_init.argtypes = [P, I]
+    L.gid_run.argtypes = [P, I, I]
+    L.gid_get_layers.argtypes = [P, P, P]
+    L.gid_get_state.argtypes = [P, P]
+    L.gid_set_state.argtypes = [P, P]
+    L.gid_energy.argtypes = [P, D, D]
+    L.gid_solve_frame_host.argtypes = [P, P, P, I, I, I, P, P, P]
+    L.gid_stage_precompute.argtypes = [P, P, P, P]
+    L.gid_stage_linearize.argtypes = [P, P, P]
+    L.gid_stage_apply.argtypes = [P, P, P]
+    L.gid_stage_pcg.argtypes = [P, I, P]
+    L.gid_stage_dense_normal.argtypes = [P, D, D]
+    L.gid_launch_count.argtypes = [P, LL]
+    L.gid_profile.argtypes = [P, I]
+    L.gid_profile_read.argtypes = [P, D, LL]
+    for n in EXPORTS:
+        if n not in ("gid_default_weights", "gid_destroy", "gid_last_error"):
+            getattr(L, n).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def default_weights(spatial_offsets=None, temporal_offsets=None, **overrides) -> Weights:
+    """gid_default_weights() plus pair offsets ((n, 2) int arrays of (dy, dx)) and overrides."""
+    w = Weights()
+    load().gid_default_weights(ctypes.byref(w))
+    if spatial_offsets is not None:
+        so = np.asarray(spatial_offsets, np.int32).reshape(-1, 2)
+        w.n_spatial_pairs = len(so)
+        for i, v in enumerate(so.ravel()):
+            w.spatial_offsets[i] = int(v)
+    if temporal_offsets is not None:
+        to = np.asarray(temporal_offsets, np.int32).reshape(-1, 2)
+        w.n_temporal_pairs = len(to)
+        for i, v in enumerate(to.ravel()):
+            w.temporal_offsets[i] = int(v)
+    for k, v in overrides.items():
+        setattr(w, k, v)
+    return w
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Solver:
+    """One gid_ctx: H x W frames, K base colours, on the current CUDA device."""
+
+    def __init__(self, H: int, W: int, K: int, weights: Weights | None = None, stream=None):
+        import torch
+        self.torch = torch
+        self.H, self.W, self.K, self.V = H, W, K, K + 4
+        self.lib = load()
+        self.weights = weights if weights is not None else default_weights()
+        h = ctypes.c_void_p()
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        rc = self.lib.gid_create(H, W, K, ctypes.byref(self.weights), s, ctypes.byref(h))
+        if rc != GID_OK:
+            raise GidError(rc, self.lib.gid_last_error(None).decode())
+        self.h = h
+
+    def _chk(self, rc):
+        if rc != GID_OK:
+            raise GidError(rc, self.lib.gid_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gid_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _dev(self, shape, dtype=None):
+        t = self.torch
+        return t.empty(shape, dtype=dtype or t.float32, device="cuda")
+
+    def _check_dev(self, x, shape, dtype):
+        t = self.torch
+        assert isinstance(x, t.Tensor) and x.is_cuda and x.is_contiguous(), "need a contiguous CUDA tensor"
+        assert tuple(x.shape) == tuple(shape) and x.dtype == dtype, (tuple(x.shape), shape, x.dtype, dtype)
+
+    # -- colours
+    def set_base_colors(self, b):
+        b = np.ascontiguousarray(b, dtype=np.float32).reshape(self.K, 3)
+        self._chk(self.lib.gid_set_base_colors(self.h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def base_colors(self) -> np.ndarray:
+        b = np.zeros((self.K, 3), np.float32)
+        self._chk(self.lib.gid_get_base_colors(self.h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return b
+
+    # -- frame / state
+    def set_frame(self, rgb, labels):
+        self._check_dev(rgb, (3, self.H, self.W), self.torch.float32)
+        self._check_dev(labels, (self.H, self.W), self.torch.uint8)
+        self._chk(self.lib.gid_set_frame(self.h, _ptr(rgb), _ptr(labels)))
+
+    def init(self, mode: int = 0):
+        self._chk(self.lib.gid_init(self.h, mode))
+
+    def run(self, n_outer: int, m_inner: int):
+        self._chk(self.lib.gid_run(self.h, n_outer, m_inner))
+
+    def layers(self, R=None, T=None):
+        R = self._dev((3, self.H, self.W)) if R is None else R
+        T = self._dev((self.K + 1, self.H, self.W)) if T is None else T
+        self._chk(self.lib.gid_get_layers(self.h, _ptr(R), _ptr(T)))
+        return R, T
+
+    def state(self):
+        X = self._dev((self.V, self.H, self.W))
+        self._chk(self.lib.gid_get_state(self.h, _ptr(X)))
+        return X
+
+    def set_state(self, X):
+        self._check_dev(X, (self.V, self.H, self.W), self.torch.float32)
+        self._chk(self.lib.gid_set_state(self.h, _ptr(X)))
+
+    def energy(self):
+        tot = ctypes.c_double()
+        per = (ctypes.c_double * 8)()
+        self._chk(self.lib.gid_energy(self.h, ctypes.byref(tot), per))
+        return tot.value, np.array(per[:])
+
+    def solve_frame_host(self, rgb, labels, init_mode, n_outer, m_inner, R=None, T=None, b=None):
+        """Host-buffer entry point; rgb/labels/R/T/b are numpy (ideally pinned) arrays."""
+        def p(a):
+            return None if a is None else ctypes.c_void_p(a.ctypes.data)
+        self._chk(self.lib.gid_solve_frame_host(self.h, p(rgb), p(labels), init_mode, n_outer, m_inner,
+                                                p(R), p(T), p(b)))
+
+    # -- stages
+    def stage_precompute(self):
+        wsr = self._dev((self.H, self.W))
+        ns, nt = self.weights.n_spatial_pairs, self.weights.n_temporal_pairs
+        ws = self._dev((max(ns, 1), self.H, self.W))
+        wt = self._dev((max(nt, 1), self.H, self.W))
+        self._chk(self.lib.gid_stage_precompute(self.h, _ptr(wsr), _ptr(ws) if ns else None, _ptr(wt) if nt else None))
+        return wsr, ws[:ns], wt[:nt]
+
+    def stage_linearize(self):
+        g, d = self._dev((self.V, self.H, self.W)), self._dev((self.V, self.H, self.W))
+        self._chk(self.lib.gid_stage_linearize(self.h, _ptr(g), _ptr(d)))
+        return g, d
+
+    def stage_apply(self, p):
+        self._check_dev(p, (self.V, self.H, self.W), self.torch.float32)
+        q = self._dev((self.V, self.H, self.W))
+        self._chk(self.lib.gid_stage_apply(self.h, _ptr(p), _ptr(q)))
+        return q
+
+    def stage_pcg(self, m_inner):
+        d = self._dev((self.V, self.H, self.W))
+        self._chk(self.lib.gid_stage_pcg(self.h, m_inner, _ptr(d)))
+        return d
+
+    def stage_dense_normal(self):
+        A = np.zeros((3, self.K, self.K))
+        g = np.zeros((3, self.K))
+        D = ctypes.POINTER(ctypes.c_double)
+        self._chk(self.lib.gid_stage_dense_normal(self.h, A.ctypes.data_as(D), g.ctypes.data_as(D)))
+        return A, g
+
+    # -- instrumentation
+    def launch_count(self) -> int:
+        n = ctypes.c_longlong()
+        self._chk(self.lib.gid_launch_count(self.h, ctypes.byref(n)))
+        return n.value
+
+    def profile(self, enable: bool):
+        self._chk(self.lib.gid_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        """{kind: (total ms, launches)} since the previous read."""
+        ms = (ctypes.c_double * len(KINDS))()
+        n = (ctypes.c_longlong * len(KINDS))()
+        self._chk(self.lib.gid_profile_read(self.h, ms, n))
+        return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}

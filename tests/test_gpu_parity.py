@@ -1,0 +1,205 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Stage checks (one kernel each) use the same float32-rounded inputs and state on
+both sides.  Their tolerance is derived from the arithmetic: every output is a
+sum of at most ~40 FP32 products, so its rounding error is below
+40 * 2^-24 * (largest summand) ~ 2.4e-6 of the largest magnitude in the field;
+the tests allow 2e-5 of the field's max (an 8x margin).  The end-to-end checks
+use the solver's bar: every layer within 1e-3 max-abs after the same N x M
+iterations from the same start, energy within 1e-4 relative.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from harness import Case
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+CASES = {
+    "64x48_K4": dict(H=48, W=64, K=4, n_cells=12),      # the 64 x 48 single-frame workload: 2 x 6 tiles
+    "37x29_K3": dict(H=29, W=37, K=3, n_cells=7),       # ragged: partial tiles in x and y
+    "70x41_K6": dict(H=41, W=70, K=6, n_cells=9),
+}
+STAGE_TOL = 2e-5
+
+
+def f32(a):
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def close(gpu, ref, tol=STAGE_TOL, what=""):
+    gpu = np.asarray(gpu, np.float64)
+    ref = np.asarray(ref, np.float64)
+    assert gpu.shape == ref.shape, (gpu.shape, ref.shape)
+    err = np.abs(gpu - ref).max()
+    scale = max(np.abs(ref).max(), 1e-30)
+    assert err <= tol * scale, f"{what}: max err {err:.3e} vs scale {scale:.3e} (rel {err / scale:.3e})"
+
+
+def random_state(case, pb, seed):
+    rng = np.random.default_rng(seed)
+    X = pb.init_cold()
+    X[:3] += rng.normal(0, 0.2, size=X[:3].shape)
+    X[3:] += rng.normal(0, 0.05, size=X[3:].shape)
+    return f32(X)
+
+
+@pytest.fixture(params=list(CASES))
+def setup(request):
+    case = Case(**CASES[request.param], seed=3)
+    s = case.solver()
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    pb = case.oracle_problem()
+    return case, s, pb
+
+
+def test_precompute(setup):
+    case, s, pb = setup
+    wsr, ws, _ = s.stage_precompute()
+    torch.cuda.synchronize()
+    close(wsr.cpu().numpy(), pb.wsr, what="w_SR")
+    close(ws.cpu().numpy(), pb.omega_s, what="omega spatial")
+
+
+def test_linearize_apply_energy(setup):
+    case, s, pb = setup
+    X = random_state(case, pb, 1)
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    g, d = s.stage_linearize()
+    close(g.cpu().numpy(), pb.rhs(X), what="-J^T F")
+    close(d.cpu().numpy(), pb.diag(X), what="diag J^T J")
+    p = np.random.default_rng(2).normal(size=X.shape).astype(np.float32)
+    q = s.stage_apply(torch.from_numpy(p).cuda())
+    close(q.cpu().numpy(), pb.apply(X, f32(p)), what="J^T J p")
+    tot, per = s.energy()
+    E = pb.energy(X)
+    for t in range(8):
+        assert per[t] == pytest.approx(E[t], rel=2e-5, abs=1e-6 * E.sum()), O.TERMS[t]
+    assert tot == pytest.approx(E.sum(), rel=2e-5)
+
+
+def test_dense_normal_equations(setup):
+    case, s, pb = setup
+    X = random_state(case, pb, 4)
+    X[4:] = np.abs(X[4:])
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    A, g = s.stage_dense_normal()
+    Ao, go = pb.dense_normal(X)
+    close(A, Ao, 1e-5, "A")
+    close(g, go, 1e-4, "g")
+
+
+def test_pcg_update(setup):
+    """delta after 10 PCG steps from the same state: rounding grows with the
+    Krylov recursion, so the bar is 1e-4 of max |delta|."""
+    case, s, pb = setup
+    X = random_state(case, pb, 5)
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    delta = s.stage_pcg(10)
+    ref, _ = pb.pcg(X, 10)
+    close(delta.cpu().numpy(), ref, 1e-4, "PCG delta")
+
+
+def run_both(case, N, M, t=0):
+    s = case.solver()
+    rgb, lab = case.gpu_inputs(t)
+    s.set_frame(rgb, lab)
+    s.init(0)
+    s.run(N, M)
+    R, T = s.layers()
+    tot, per = s.energy()
+    b = s.base_colors()
+    pb = case.oracle_problem(t)
+    Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), N, M)
+    return (R.cpu().numpy(), T.cpu().numpy(), b, tot), (np.exp(Xo[:3]), Xo[3:], bo, hist[-1].sum())
+
+
+@pytest.mark.parametrize("name", ["64x48_K4", "37x29_K3"])
+def test_end_to_end_single_frame(name):
+    """The 64x48 K=4 workload: 5 Gauss-Newton x 10 PCG, cold start, refinement on."""
+    case = Case(**CASES[name], seed=0)
+    (R, T, b, E), (Ro, To, bo, Eo) = run_both(case, 5, 10)
+    assert np.abs(R - Ro).max() <= 1e-3
+    for k in range(case.K + 1):
+        assert np.abs(T[k] - To[k]).max() <= 1e-3, k
+    assert np.abs(b - bo).max() <= 1e-3
+    assert E == pytest.approx(Eo, rel=1e-4)
+
+
+def test_end_to_end_two_frames_temporal():
+    """Frame 0 cold, frame 1 warm with temporal pairs to frame 0 (3 x 8 each)."""
+    case = Case(H=48, W=64, K=4, n_cells=12, seed=1, frames=2, temporal=True)
+    s = case.solver()
+    pb0 = case.oracle_problem(0)
+    X0, b0, _ = O.solve_frame(pb0, pb0.init_cold(), 3, 8)
+    for t in range(2):
+        rgb, lab = case.gpu_inputs(t)
+        s.set_frame(rgb, lab)
+        s.init(0 if t == 0 else 1)
+        s.run(3, 8)
+    R, T = s.layers()
+    b = s.base_colors()
+    E, _ = s.energy()
+    pb1 = case.oracle_problem(1, rprev=X0[:3], b=b0)
+    X1, b1, hist = O.solve_frame(pb1, X0, 3, 8)
+    assert np.abs(R.cpu().numpy() - np.exp(X1[:3])).max() <= 1e-3
+    assert np.abs(T.cpu().numpy() - X1[3:]).max() <= 1e-3
+    assert np.abs(b - b1).max() <= 1e-3
+    assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+def test_host_buffer_entry_point_matches_device_path():
+    case = Case(**CASES["37x29_K3"], seed=2)
+    s1 = case.solver()
+    rgb, lab = case.gpu_inputs()
+    s1.set_frame(rgb, lab)
+    s1.init(0)
+    s1.run(2, 5)
+    R1, T1 = s1.layers()
+    s2 = case.solver()
+    f = case.frames[0]
+    R2 = np.zeros((3, case.H, case.W), np.float32)
+    T2 = np.zeros((case.K + 1, case.H, case.W), np.float32)
+    b2 = np.zeros((case.K, 3), np.float32)
+    s2.solve_frame_host(np.ascontiguousarray(f.I, np.float32), np.ascontiguousarray(f.labels, np.uint8), 0, 2, 5,
+                        R2, T2, b2)
+    assert np.array_equal(R1.cpu().numpy(), R2) and np.array_equal(T1.cpu().numpy(), T2)
+    assert np.array_equal(s1.base_colors(), b2)
+
+
+def test_runs_are_bitwise_reproducible():
+    case = Case(**CASES["70x41_K6"], seed=4)
+    out = []
+    for _ in range(2):
+        s = case.solver()
+        rgb, lab = case.gpu_inputs()
+        s.set_frame(rgb, lab)
+        s.init(0)
+        s.run(2, 6)
+        out.append(s.state().cpu().numpy())
+    assert np.array_equal(out[0], out[1])
+
+
+def test_errors_are_reported():
+    from paper_1908_01961_b300 import gid
+    case = Case(**CASES["37x29_K3"], seed=2)
+    s = case.solver()
+    with pytest.raises(gid.GidError) as e:
+        s.run(1, 1)
+    assert e.value.code == -4
+    with pytest.raises(gid.GidError) as e:
+        gid.Solver(8, 8, 11)
+    assert e.value.code == -1
+    rgb, lab = case.gpu_inputs()
+    lab[0, 0] = case.K                                    # out-of-range label
+    s.set_frame(rgb, lab)
+    s.init(0)
+    with pytest.raises(gid.GidError) as e:
+        s.energy()
+    assert e.value.code == -1
+    with pytest.raises(gid.GidError):
+        s.set_base_colors(np.zeros((case.K, 3)))
