@@ -1,0 +1,353 @@
+"""Benchmark: frames/s of the per-frame decomposition solve on a 640x480, K=6 video.
+
+One step = one pass of the whole hot path over one synthetic 30-frame video:
+every frame is ingested (chromaticity, soft-Retinex weight, pair weights), the
+first is cold-started and the others warm-started from the previous frame, and
+each frame runs 8 outer iterations of (Gauss-Newton step with 20 PCG steps,
+then the base-colour step), temporal pairs on.  Inputs are resident in HBM;
+L2 is flushed (256 MB write) before every step, outside the timed events.
+
+Prints one JSON line (rank 0).  Under torchrun every rank solves its own video
+(weak scaling, no data-path collective); the time is the max over ranks.
+`--impl reference` times the FP64 CPU oracle instead, on a bounded sample.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_1908_01961_b300 import synth  # noqa: E402
+
+WORK = synth.VIDEO_640x480
+METRIC = "frames/s at 640x480 K=6 (plain cold/warm solve, 8 GN x 20 PCG per frame)"
+WORKLOAD = ("video_640x480_K6: 30 synthetic frames, 40 moving Voronoi cells, rotating light; "
+            "frame 0 cold start, frames 1-29 warm start; 8 outer x (GN step of 20 PCG + base-colour step); "
+            "temporal + 4 spatial consistency pairs")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gid", choices=["gid", "reference"])
+    ap.add_argument("--frames", type=int, default=WORK["frames"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    return ap.parse_args()
+
+
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def make_video(seed, frames):
+    v = synth.SyntheticVideo(WORK["H"], WORK["W"], WORK["K"], WORK["n_cells"], seed=seed)
+    fr = [v.frame(t) for t in range(frames)]
+    b0 = synth.initial_base_colors(fr[0].I, fr[0].labels, WORK["K"]).astype(np.float32)
+    return fr, b0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, dev):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(dev)], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        self.p.wait()
+        self.f.flush()
+        rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        if os.path.isdir(os.path.join(ROOT, "gpurun_out")):
+            with open(os.path.join(ROOT, "gpurun_out", "clocks.csv"), "w") as g:
+                g.write("\n".join(", ".join(r) for r in rows) + "\n")
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def source_hash():
+    h = hashlib.sha256()
+    d = os.path.join(ROOT, "paper_1908_01961_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        h.update(open(os.path.join(d, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it was
+    taken on the current sources (else None)."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            t = json.load(f)
+        if t.get("source_hash") != source_hash():
+            return None
+        return t["kernels"][kernel]["dram_bytes_per_launch_full_size"]
+    except Exception:
+        return None
+
+
+def algorithmic_bytes(kind, K, P, M, ns, nt, temporal):
+    """Minimum bytes each kernel kind must move per launch (FP32 planes)."""
+    V = K + 4
+    t = 1 if temporal else 0
+    if kind == "apply":     # read z, p_old, X, w_SR, pair weights, temporal sum; write p, q
+        first = 4 * V + 2 + ns + t
+        rest = 5 * V + 2 + ns + t
+        return 4.0 * P * ((M - 1) * rest + first) / M
+    if kind == "update":    # read delta, p, q, r, M^-1; write delta, r, z (last: read delta, p, X; write X)
+        return 4.0 * P * ((M - 1) * 8 * V + 4 * V) / M
+    if kind == "linearize":  # read X, I, w_SR, pairs (+ r_prev); write M^-1, r, z, delta; labels 1 B
+        return 4.0 * P * (5 * V + 4 + ns + nt * t + 3 * t) + P
+    if kind == "dense":     # read X and I
+        return 4.0 * P * (V + 3)
+    return None
+
+
+# ---------------------------------------------------------------- reference arm (the oracle)
+
+def cpu_sample(seed=0):
+    """The FP64 oracle on one 640x480 frame, 1 of the 8 outer iterations (GN step
+    of 20 PCG + base-colour step), cold start; returns (seconds, frames/s)."""
+    import oracle as O
+    fr, b0 = make_video(seed, 1)
+    off_s, _ = synth.offsets_for(seed)
+    I = fr[0].I.astype(np.float32).astype(np.float64)
+    t0 = time.perf_counter()
+    C, wsr, om, _ = O.precompute(I, off_s)
+    pb = O.Problem(I, fr[0].labels, b0.astype(np.float64), wsr, om, off_s)
+    O.solve_frame(pb, pb.init_cold(), 1, WORK["M"])
+    dt = time.perf_counter() - t0
+    return dt, 1.0 / (WORK["N"] * dt)
+
+
+CPU_SAMPLE = ("one 640x480 K=6 frame, 1 of its 8 outer iterations (precompute + GN step of 20 PCG + "
+              "base-colour step), FP64 oracle, 1 thread; frames/s = 1 / (8 x time)")
+
+
+def run_reference(args, ws, rank):
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    for _ in range(args.warmup):
+        cpu_sample(0)
+    times = [cpu_sample(0)[0] for _ in range(args.steps)]
+    tot = sum(times)
+    value = args.steps / (WORK["N"] * tot)
+    out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "config": {"workload": WORKLOAD, "H": WORK["H"], "W": WORK["W"], "K": WORK["K"],
+                      "step": "1/8 of one frame (one outer iteration), scaled to frames/s"},
+           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE},
+           "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- CUDA arm
+
+def run_gid(args, ws, rank, local):
+    import torch
+
+    from paper_1908_01961_b300 import gid
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H, W, K, N, M, F = WORK["H"], WORK["W"], WORK["K"], WORK["N"], WORK["M"], args.frames
+    P = H * W
+    seed = rank
+    frames, b0 = make_video(seed, F)
+    off_s, off_t = synth.offsets_for(seed)
+    rgb = [torch.from_numpy(f.I.astype(np.float32)).to(dev) for f in frames]
+    lab = [torch.from_numpy(f.labels).to(dev) for f in frames]
+    w = gid.default_weights(off_s, off_t, temporal=1)
+    s = gid.Solver(H, W, K, w)
+    s.set_base_colors(b0)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)   # 256 MB > 126 MB L2
+
+    def step():
+        s.new_sequence()
+        for t in range(F):
+            s.set_frame(rgb[t], lab[t])
+            s.init(0 if t == 0 else 1)
+            s.run(N, M)
+
+    for _ in range(args.warmup):
+        flush.fill_(1.0)
+        step()
+    torch.cuda.synchronize()
+    # timed region
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    n0 = s.launch_count()
+    for i in range(args.steps):
+        flush.fill_(float(i))
+        ev[i][0].record(stream)
+        step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = s.launch_count() - n0
+    clk = clocks.stop()
+    ms = [a.elapsed_time(b) for a, b in ev]
+    total_ms = max_over_ranks(ws, sum(ms))
+    value = ws * args.steps * F / (total_ms / 1000.0)
+    E, _ = s.energy()
+    if not np.isfinite(E):
+        raise RuntimeError("non-finite energy after the timed steps")
+
+    # one profiled step (identical work): per-kernel CUDA-event durations on the ctx stream
+    flush.fill_(0.0)
+    s.profile(True)
+    step()
+    prof = s.profile_read()
+    s.profile(False)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms = kinds[dom][0] / kinds[dom][1]
+    alg = algorithmic_bytes(dom, K, P, M, len(off_s), len(off_t), True)
+    peak, peak_src = measured_peaks()
+    kernel_name = {"apply": "k_apply", "update": "k_update", "linearize": "k_linearize", "dense": "k_dense"}.get(dom)
+    traffic = ncu_traffic(kernel_name) if kernel_name else None
+    roof = None
+    if alg:
+        ach = alg / (dom_ms / 1000.0) / 1e9
+        roof = {"bound": "hbm", "kernel": kernel_name, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": ach / peak, "traffic": traffic, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_ms}
+    shares = {k: {"ms_per_step": v[0], "launches": v[1]} for k, v in kinds.items()}
+
+    # end to end: the host-buffer entry point, host<->device copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        rgb_h = [torch.from_numpy(f.I.astype(np.float32)).pin_memory().numpy() for f in frames]
+        lab_h = [torch.from_numpy(f.labels.copy()).pin_memory().numpy() for f in frames]
+        R_h = torch.empty((3, H, W), dtype=torch.float32).pin_memory().numpy()
+        T_h = torch.empty((K + 1, H, W), dtype=torch.float32).pin_memory().numpy()
+        b_h = np.zeros((K, 3), np.float32)
+
+        def e2e_step():
+            s.new_sequence()
+            for t in range(F):
+                s.solve_frame_host(rgb_h[t], lab_h[t], 0 if t == 0 else 1, N, M, R_h, T_h, b_h)
+
+        e2e_step()
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        dt = max_over_ranks(ws, time.perf_counter() - t0)
+        e2e = {"value": ws * args.steps * F / dt, "unit": "frames/s",
+               "h2d_bytes_per_step": F * (3 * P * 4 + P),
+               "d2h_bytes_per_step": F * ((3 + K + 1) * P * 4 + K * 3 * 4)}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        dt, fps = cpu_sample(0)
+        cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE,
+               "seconds": dt}
+
+    if rank == 0:
+        out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
+               "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+               "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": WORKLOAD, "H": H, "W": W, "K": K, "frames_per_step": F, "N_outer": N,
+                          "M_inner": M, "l2": "flushed before each step (256 MB write, outside the events)",
+                          "parallelism": f"replicas x{ws} (one video per GPU)"},
+               "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
+               "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E}
+        print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+    else:
+        run_gid(args, ws, rank, local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

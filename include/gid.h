@@ -105,6 +105,11 @@ int gid_get_base_colors(gid_ctx* ctx, float* b_host);
  * >= K are reported as GID_ERR_INVALID_ARG by the next synchronising call. */
 int gid_set_frame(gid_ctx* ctx, const float* rgb_dev, const uint8_t* labels_dev);
 
+/* Start a new video on this context: forget the previous frame (the next frame
+ * gets no temporal pairs), reset the refined base colours to the initial ones
+ * and count the next frame as the first (refine_base_colors = 2).  Async. */
+int gid_new_sequence(gid_ctx* ctx);
+
 /* Initial state: mode 0 = cold start (r = ln R_cluster, T_0 = mean_c I /
  * mean_c R_cluster, T_k = 0), mode 1 = warm start (keep the previous frame's
  * layers and base colours; needs a solved frame).  Requires gid_set_frame. */
@@ -180,7 +185,7 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 int gid_launch_count(const gid_ctx* ctx, long long* n);
 
 /* enable != 0: bracket every later kernel launch with CUDA events on the
- * context stream (up to 8192 launches between reads); 0 stops recording. */
+ * context stream (up to 16384 launches between reads); 0 stops recording. */
 int gid_profile(gid_ctx* ctx, int enable);
 
 /* Synchronise and return, per kind, the summed device time (ms[GID_NUM_KINDS])

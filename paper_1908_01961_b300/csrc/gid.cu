@@ -385,6 +385,16 @@ extern "C" int gid_set_frame(gid_ctx* c, const float* rgb_dev, const uint8_t* la
   return GID_OK;
 }
 
+extern "C" int gid_new_sequence(gid_ctx* c) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  launch(c, GID_KIND_INIT, [&] { k_reset_colors<<<1, 32, 0, c->stream>>>(c->col, 3 * c->K); });
+  if (int rc = check_launch(c, "k_reset_colors")) return rc;
+  c->frames_solved = 0;
+  c->temporal_active = false;
+  c->initialised = false;
+  return GID_OK;
+}
+
 extern "C" int gid_init(gid_ctx* c, int mode) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (!c->has_frame || !c->has_colors)
@@ -579,7 +589,7 @@ extern "C" int gid_launch_count(const gid_ctx* c, long long* n) {
 extern "C" int gid_profile(gid_ctx* c, int enable) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (enable && c->ev.empty()) {
-    c->ev.resize(2 * 8192);
+    c->ev.resize(2 * 16384);
     for (auto& e : c->ev) GID_TRY_CUDA(c, cudaEventCreate(&e));
   }
   c->prof = enable != 0;

@@ -303,6 +303,15 @@ __global__ void k_prior_weights(Params P, const float* __restrict__ C, const flo
   }
 }
 
+// Refined base colours back to the initial estimate.
+__global__ void k_reset_colors(DevColors* col, int n) {
+  const int i = threadIdx.x;
+  if (i < n) {
+    col->b[i] = col->binit[i];
+    col->bd[i] = (double)col->binit[i];
+  }
+}
+
 // Cold start: r = ln R_cluster, T_0 = mean_c I / mean_c R_cluster, T_k = 0.
 template <int K>
 __global__ void k_init_cold(Params P) {

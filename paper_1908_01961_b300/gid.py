@@ -29,7 +29,7 @@ EXPORTS = (
     "gid_get_base_colors", "gid_set_frame", "gid_init", "gid_run", "gid_get_layers", "gid_get_state",
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
-    "gid_profile_read",
+    "gid_profile_read", "gid_new_sequence",
 )
 
 
@@ -75,6 +75,7 @@ def load():
     L.gid_get_base_colors.argtypes = [P, F]
     L.gid_set_frame.argtypes = [P, P, P]
     L.gid_init.argtypes = [P, I]
+    L.gid_new_sequence.argtypes = [P]
     L.gid_run.argtypes = [P, I, I]
     L.gid_get_layers.argtypes = [P, P, P]
     L.gid_get_state.argtypes = [P, P]
@@ -176,6 +177,9 @@ class Solver:
         self._check_dev(rgb, (3, self.H, self.W), self.torch.float32)
         self._check_dev(labels, (self.H, self.W), self.torch.uint8)
         self._chk(self.lib.gid_set_frame(self.h, _ptr(rgb), _ptr(labels)))
+
+    def new_sequence(self):
+        self._chk(self.lib.gid_new_sequence(self.h))
 
     def init(self, mode: int = 0):
         self._chk(self.lib.gid_init(self.h, mode))
