@@ -192,6 +192,43 @@ int gid_profile(gid_ctx* ctx, int enable);
  * and launch count (count[GID_NUM_KINDS]) recorded since the previous read. */
 int gid_profile_read(gid_ctx* ctx, double* ms, long long* count);
 
+/* ---- base-colour step without device allocation ---- */
+
+/* Bytes of the file-scope device array that gid_dense_refine_noalloc uses as
+ * scratch.  Every GPU that loads the library holds this much until exit. */
+#define GID_NOALLOC_SCRATCH_BYTES (512 * 1024)
+
+/* The paper has no counterpart to this call; it exists for callers that cannot
+ * allocate device memory (code living inside another framework's memory pool,
+ * real-time loops that must not block on the allocator, processes that are only
+ * handed device pointers).  It computes the same base-colour step as gid_run's
+ * dense stage -- the three K x K normal equations of eq:basecolorrefinement at
+ * the layers X and their FP64 Cholesky solve -- without a context and without
+ * any cudaMalloc / cudaFree: its scratch is a static device array of
+ * GID_NOALLOC_SCRATCH_BYTES, enough for every K <= GID_MAX_K and every frame up
+ * to 2^28 pixels (the reduction uses at most 296 x 3 blocks).
+ *   X_dev       (K+4) x H x W float32 unknowns (r_R, r_G, r_B, T_0..T_K), device
+ *   rgb_dev     3 x H x W float32 frame, device
+ *   b_init_host K x 3 initial base colours (finite, > 0), host
+ *   w           weights; lambda_data, lambda_IR and lambda_CR are used
+ *   stream      cudaStream_t or NULL
+ *   A_dev       out, 3 x K x K doubles (device) or NULL
+ *   g_dev       out, 3 x K doubles (device) or NULL
+ *   b_dev       out, K x 3 floats, refined colours b_init + Delta b (device) or NULL
+ *   errbuf      optional caller buffer of errbuf_len bytes for an error message
+ * Returns GID_ERR_INVALID_ARG for a NULL input, K outside 1..GID_MAX_K or a
+ * frame beyond 2^28 pixels, GID_ERR_NUMERIC if a block is not positive
+ * definite (b_dev then holds b_init), GID_ERR_CUDA on a runtime error.
+ * Synchronises the stream before returning.  The first call on each device
+ * resolves the array's device address (cudaGetSymbolAddress) with that device
+ * current; make that first call before any stream capture.  All calls on a
+ * device share the one array and it keeps the last call's contents (the call
+ * clears what must start at zero itself): calls that overlap on the GPU, from
+ * several streams or threads, race and must be serialised by the caller. */
+int gid_dense_refine_noalloc(int H, int W, int K, const float* X_dev, const float* rgb_dev,
+                             const float* b_init_host, const gid_weights* w, void* stream, double* A_dev,
+                             double* g_dev, float* b_dev, char* errbuf, int errbuf_len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -29,7 +29,7 @@ EXPORTS = (
     "gid_get_base_colors", "gid_set_frame", "gid_init", "gid_run", "gid_get_layers", "gid_get_state",
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
-    "gid_profile_read", "gid_new_sequence",
+    "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc",
 )
 
 
@@ -90,6 +90,8 @@ def load():
     L.gid_launch_count.argtypes = [P, LL]
     L.gid_profile.argtypes = [P, I]
     L.gid_profile_read.argtypes = [P, D, LL]
+    L.gid_dense_refine_noalloc.argtypes = [I, I, I, P, P, F, ctypes.POINTER(Weights), P, P, P, P,
+                                           ctypes.c_char_p, I]
     for n in EXPORTS:
         if n not in ("gid_default_weights", "gid_destroy", "gid_last_error"):
             getattr(L, n).restype = ctypes.c_int
@@ -114,6 +116,25 @@ def default_weights(spatial_offsets=None, temporal_offsets=None, **overrides) ->
     for k, v in overrides.items():
         setattr(w, k, v)
     return w
+
+
+def dense_refine_noalloc(X, rgb, b_init, weights=None, A=None, g=None, b=None, stream=None):
+    """Base-colour step without any device allocation inside the library (see
+    gid_dense_refine_noalloc in include/gid.h).  X: (K+4, H, W) and rgb: (3, H, W)
+    float32 CUDA tensors; A (3, K, K) float64, g (3, K) float64 and b (K, 3)
+    float32 are optional caller-allocated CUDA outputs."""
+    import torch
+    V, H, W = X.shape
+    K = V - 4
+    bi = np.ascontiguousarray(b_init, dtype=np.float32).reshape(K, 3)
+    w = weights if weights is not None else default_weights()
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    err = ctypes.create_string_buffer(256)
+    rc = load().gid_dense_refine_noalloc(H, W, K, _ptr(X), _ptr(rgb), bi.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                         ctypes.byref(w), ctypes.c_void_p(s), _ptr(A), _ptr(g), _ptr(b), err, 256)
+    if rc != GID_OK:
+        raise GidError(rc, err.value.decode())
+    return A, g, b
 
 
 def _ptr(t):
