@@ -160,17 +160,18 @@ def ncu_traffic(kernel):
 
 
 def algorithmic_bytes(kind, K, P, M, ns, nt, temporal):
-    """Minimum bytes each kernel kind must move per launch (FP32 planes)."""
+    """Minimum bytes each kernel kind moves per launch as designed (FP32 planes)."""
     V = K + 4
+    NC = 10 + 3 * (K + 1)          # operator coefficient planes written by k_linearize
     t = 1 if temporal else 0
-    if kind == "apply":     # read z, p_old, X, w_SR, pair weights, temporal sum; write p, q
-        first = 4 * V + 2 + ns + t
-        rest = 5 * V + 2 + ns + t
+    if kind == "apply":     # read z, coefficients, pair weights (+ p_old, q_old after step 1); write p, q
+        first = 3 * V + NC + ns
+        rest = 5 * V + NC + ns
         return 4.0 * P * ((M - 1) * rest + first) / M
     if kind == "update":    # read delta, p, q, r, M^-1; write delta, r, z (last: read delta, p, X; write X)
         return 4.0 * P * ((M - 1) * 8 * V + 4 * V) / M
-    if kind == "linearize":  # read X, I, w_SR, pairs (+ r_prev); write M^-1, r, z, delta; labels 1 B
-        return 4.0 * P * (5 * V + 4 + ns + nt * t + 3 * t) + P
+    if kind == "linearize":  # read X, I, w_SR, pairs (+ r_prev, temporal sum); write M^-1, r, z, delta, coefficients
+        return 4.0 * P * (5 * V + 4 + ns + (nt + 3 + 1) * t + NC) + P
     if kind == "dense":     # read X and I
         return 4.0 * P * (V + 3)
     return None

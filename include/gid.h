@@ -74,7 +74,7 @@ typedef struct gid_ctx gid_ctx;
 void gid_default_weights(gid_weights* w);
 
 /* Create a solver for H x W frames with K base colours (1 <= K <= GID_MAX_K,
- * H, W >= 1).  Allocates about (8 (K + 4) + 22) planes of H x W floats on the
+ * H, W >= 1).  Allocates about (11 K + 67) planes of H x W floats on the
  * current device.  stream: a cudaStream_t or NULL.  On success *out owns the
  * context; on failure *out is NULL and the code says why (GID_ERR_OOM,
  * GID_ERR_CUDA, GID_ERR_INVALID_ARG). */

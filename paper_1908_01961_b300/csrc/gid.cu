@@ -26,7 +26,7 @@ struct gid_ctx {
         *wtsum = nullptr;
   uint8_t* lab = nullptr;
   float *X = nullptr, *d = nullptr, *r = nullptr, *z = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr,
-        *Minv = nullptr;
+        *Minv = nullptr, *coef = nullptr;
   DevColors* col = nullptr;
   DevScalars* sc = nullptr;
   double* partial = nullptr;
@@ -129,6 +129,7 @@ static Params params(const gid_ctx* c) {
   P.z = c->z;
   P.q = c->q;
   P.Minv = c->Minv;
+  P.coef = c->coef;
   P.col = c->col;
   P.sc = c->sc;
   P.partial = c->partial;
@@ -150,10 +151,18 @@ struct Launch {
     k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg);
   }
   static void apply(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
-    k_apply<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, first, pin, pout, qout);
+    static bool attr = false;  // opt in to > 48 KB of dynamic shared memory once per instantiation
+    const size_t smem = sizeof(ApplyTile<K>);
+    if (!attr) {
+      cudaFuncSetAttribute(k_apply<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      attr = true;
+    }
+    const dim3 grid((c->W + VTW - 1) / VTW, (c->H + BY - 1) / BY);
+    k_apply<K><<<grid, dim3(BX, BY), smem, c->stream>>>(params(c), mode, first, pin, pout, qout);
   }
   static void update(const gid_ctx* c, const float* p, int last) {
-    k_update<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), p, last);
+    const long n4 = c->plane / 4;
+    k_update<K><<<dim3((unsigned)((n4 + 255) / 256), K + 4), 256, 0, c->stream>>>(params(c), p, last);
   }
   static void dense(const gid_ctx* c, int solve) {
     k_dense<K><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
@@ -263,12 +272,13 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->pitch = (W + 31) / 32 * 32;
   c->plane = (long)H * c->pitch;
   const int ns = std::max(1, w->n_spatial_pairs), nt = std::max(1, w->n_temporal_pairs);
-  // planes: I 3, C 3, Cprev 3, rprev 3, wsr 1, ws ns, wt nt, wtsum 1, X d r z pA pB q Minv 8V
-  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V;
+  // planes: I 3, C 3, Cprev 3, rprev 3, wsr 1, ws ns, wt nt, wtsum 1, X d r z pA pB q Minv 8V, coefficients
+  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V + coef_planes(K);
   const size_t fbytes = (size_t)nplanes * c->plane * sizeof(float) + 256 * (size_t)nplanes;
   const size_t lbytes = ((size_t)c->plane + 255) / 256 * 256;
   const long nb = (long)pix_grid(c).x * pix_grid(c).y;
-  const long npart = std::max(nb * 8, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K));
+  const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
+  const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
   const size_t pbytes = (size_t)npart * sizeof(double);
   c->pool_bytes = fbytes + lbytes + 256 * 8 + sizeof(DevColors) + sizeof(DevScalars) + pbytes;
   e = cudaMalloc(&c->pool, c->pool_bytes);
@@ -299,6 +309,7 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->pB = planes(c->V);
   c->q = planes(c->V);
   c->Minv = planes(c->V);
+  c->coef = planes(coef_planes(K));
   c->lab = (uint8_t*)take(lbytes);
   c->col = (DevColors*)take(sizeof(DevColors));
   c->sc = (DevScalars*)take(sizeof(DevScalars));
@@ -414,13 +425,10 @@ extern "C" int gid_init(gid_ctx* c, int mode) {
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
   if (int rc = check_launch(c, "k_linearize")) return rc;
-  float* pin = c->pB;
-  float* pout = c->pA;
+  // p and q are updated in place (see k_apply)
   for (int m = 1; m <= m_inner; m++) {
-    launch(c, GID_KIND_APPLY, [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, (const float*)pin, pout, c->q); });
-    launch(c, GID_KIND_UPDATE,
-           [&] { GID_DISPATCH(c, update, c, (const float*)pout, m == m_inner ? last_mode : 0); });
-    std::swap(pin, pout);
+    launch(c, GID_KIND_APPLY, [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, (const float*)c->pA, c->pA, c->q); });
+    launch(c, GID_KIND_UPDATE, [&] { GID_DISPATCH(c, update, c, (const float*)c->pA, m == m_inner ? last_mode : 0); });
   }
   return check_launch(c, "pcg");
 }
@@ -554,6 +562,7 @@ extern "C" int gid_stage_apply(gid_ctx* c, const float* p_dev, float* q_dev) {
   if (!c || !p_dev || !q_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
   if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
   if (int rc = to_pitched(c, c->pA, p_dev)) return rc;
+  launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 2, (float*)nullptr, (float*)nullptr); });
   launch(c, GID_KIND_APPLY,
          [&] { GID_DISPATCH(c, apply, c, 1, 0, (const float*)c->pA, (float*)nullptr, c->pB); });
   if (int rc = check_launch(c, "k_apply")) return rc;

@@ -2,7 +2,8 @@
 //
 // Unknowns per pixel (V = K + 4): r_R, r_G, r_B (r = ln R) and T_0..T_K, stored
 // as V float32 planes [V][H][pitch] (pitch a multiple of 32 floats, 128-byte
-// rows).  One thread owns one pixel in the stencil kernels; blocks are 32 x 8.
+// rows).  One thread owns one pixel (or a column of pixels) in the stencil
+// kernels; blocks are 32 x 8; the element-wise PCG step works on float4.
 //
 // The Gauss-Newton normal matrix J^T J of the IRLS-reweighted energy
 // (eq:giv-energy, Sec. 5.3, Sec. 6) is never stored: every kernel that needs it
@@ -68,6 +69,7 @@ struct Params {
   float* z;
   float* q;
   float* Minv;
+  float* coef;  // operator coefficient planes written by k_linearize (CoefLayout)
   DevColors* col;
   DevScalars* sc;
   double* partial;
@@ -78,6 +80,7 @@ struct Params {
 __device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
 
 // Sum of v over the block; the result is valid in thread 0.  All threads call.
+// FP64 throughout (used for the cross-block totals).
 __device__ __forceinline__ double block_sum(double v) {
   __shared__ double sh[32];
   const int t = tid_flat(), lane = t & 31, wid = t >> 5;
@@ -87,11 +90,27 @@ __device__ __forceinline__ double block_sum(double v) {
   if (lane == 0) sh[wid] = v;
   __syncthreads();
   double s = 0.0;
-  if (wid == 0) {
-    s = lane < nw ? sh[lane] : 0.0;
+  if (t == 0)
+    for (int i = 0; i < nw; i++) s += sh[i];
+  __syncthreads();
+  return s;
+}
+
+// Block sum of per-thread FP32 partials: an FP32 shuffle tree inside each warp
+// (32 terms, pairwise), then the warp sums added in FP64 in warp order.  FP64
+// arithmetic runs at a small fraction of the FP32 rate on this part, so FP64 is
+// kept to the few cross-warp and cross-block additions.  Valid in thread 0.
+__device__ __forceinline__ double block_sum_f(float v) {
+  __shared__ double sh[32];
+  const int t = tid_flat(), lane = t & 31, wid = t >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  }
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = (double)v;
+  __syncthreads();
+  double s = 0.0;
+  if (t == 0)
+    for (int i = 0; i < nw; i++) s += sh[i];
   __syncthreads();
   return s;
 }
@@ -114,9 +133,22 @@ __device__ __forceinline__ bool last_block(unsigned int* cnt) {
 }
 
 // Sum of n partials (stride `stride`, starting at `base`) in a fixed order.
+// Loads are issued four at a time so the last block is not latency bound.
 __device__ __forceinline__ double grid_total(const double* partial, int n, int stride, int base) {
+  const int nt = blockDim.x * blockDim.y;
   double s = 0.0;
-  for (int i = tid_flat(); i < n; i += blockDim.x * blockDim.y) s += __ldcg(partial + (long)i * stride + base);
+  int i = tid_flat();
+  for (; i + 3 * nt < n; i += 4 * nt) {
+    const double a0 = __ldcg(partial + (long)i * stride + base);
+    const double a1 = __ldcg(partial + (long)(i + nt) * stride + base);
+    const double a2 = __ldcg(partial + (long)(i + 2 * nt) * stride + base);
+    const double a3 = __ldcg(partial + (long)(i + 3 * nt) * stride + base);
+    s += a0;
+    s += a1;
+    s += a2;
+    s += a3;
+  }
+  for (; i < n; i += nt) s += __ldcg(partial + (long)i * stride + base);
   return block_sum(s);
 }
 
@@ -164,6 +196,25 @@ __device__ __forceinline__ void load_colors(ColorTable<K>& t, const DevColors* c
   }
   __syncthreads();
 }
+
+// ---------------------------------------------------------------- operator coefficients
+
+// Per-pixel coefficients of J^T J at the linearisation point, one plane each,
+// written once per Gauss-Newton step by k_linearize and read by every PCG
+// operator step of that step:
+//   A  (3)     lambda_data R_c^2                  data term
+//   S  (3)     S_c = sum_k b_kc T_k               data term
+//   WR, WD     r-sparsity weight of the edge to the right / below (0 if absent)
+//   ER, ED     smoothness weight of each layer's edge to the right / below (0 if absent)
+//   WT (K+1)   non-negativity + decomposition-sparsity diagonal of each layer
+//   DR         lambda_clustering + temporal consistency diagonal of r
+//   WM         lambda_monochrome w_SR
+template <int K>
+struct CoefLayout {
+  static constexpr int A = 0, S = 3, WR = 6, WD = 7, ER = 8, ED = 8 + (K + 1), WT = 8 + 2 * (K + 1),
+                       DR = 8 + 3 * (K + 1), WM = 9 + 3 * (K + 1), N = 10 + 3 * (K + 1);
+};
+constexpr int coef_planes(int K) { return 10 + 3 * (K + 1); }
 
 // ---------------------------------------------------------------- stencil helpers
 
@@ -351,75 +402,10 @@ __device__ __forceinline__ void load_state(const Params& P, const ColorTable<K>&
   }
 }
 
-// q = (J^T J) p at one pixel.  pf(v, dy, dx) returns p at a neighbour (only
-// called for in-image neighbours).  pc holds p at the pixel.
-template <int K, class PF>
-__device__ __forceinline__ void normal_apply(const Params& P, const ColorTable<K>& ct, const Pix& px, long o,
-                                             const PixState<K>& s, const float* pc, PF pf, float* qv) {
-  constexpr int V = K + 4;
-  const Weights& w = P.w;
-#pragma unroll
-  for (int v = 0; v < V; v++) qv[v] = 0.f;
-  // E_data (eq:data-term): rank-3 block of the pixel.
-  for (int c = 0; c < 3; c++) {
-    float Pc = 0.f;
-#pragma unroll
-    for (int k = 0; k <= K; k++) Pc += ct.b[k][c] * pc[3 + k];
-    const float u = w.ld * s.R[c] * s.R[c] * (s.S[c] * pc[c] + Pc);
-    qv[c] += s.S[c] * u;
-#pragma unroll
-    for (int k = 0; k <= K; k++) qv[3 + k] += ct.b[k][c] * u;
-  }
-  // E_clustering (eq:clustering-term): diagonal.
-  for (int c = 0; c < 3; c++) qv[c] += w.lcl * pc[c];
-  // E_r-sparsity (eq:reflectance-sparsity-term): 4-neighbour stencil on r.
-  const Edges er = rsparse_edges(P, P.X, px);
-  for (int c = 0; c < 3; c++) qv[c] += edge_laplace(er, px, pc[c], [&](int dy, int dx) { return pf(c, dy, dx); });
-  // E_r-consistency, spatial pairs (x, x + o_j) and (x - o_j, x).
-  for (int j = 0; j < P.ns; j++) {
-    const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
-    if (inside(P, px.y + dy, px.x + dx)) {
-      const float of = w.lrc * P.ws[j * P.plane + o];
-      for (int c = 0; c < 3; c++) qv[c] += of * (pc[c] - pf(c, dy, dx));
-    }
-    if (inside(P, px.y - dy, px.x - dx)) {
-      const float ob = w.lrc * P.ws[j * P.plane + o - (long)dy * P.pitch - dx];
-      for (int c = 0; c < 3; c++) qv[c] += ob * (pc[c] - pf(c, -dy, -dx));
-    }
-  }
-  // E_r-consistency, temporal pairs: diagonal (the previous frame is fixed).
-  if (P.temporal) {
-    const float wt = w.lrc * P.wtsum[o];
-    for (int c = 0; c < 3; c++) qv[c] += wt * pc[c];
-  }
-  // E_monochrome (Sec. 5.2): rank-3 block on T.
-  const float wm = w.lm * P.wsr[o];
-  for (int c = 0; c < 3; c++) {
-    float m = 0.f;
-#pragma unroll
-    for (int k = 0; k <= K; k++) m += ct.dm[k][c] * pc[3 + k];
-    m *= wm;
-#pragma unroll
-    for (int k = 0; k <= K; k++) qv[3 + k] += ct.dm[k][c] * m;
-  }
-  // E_i-sparsity (k >= 1) and E_non-neg (all k): diagonal IRLS weights.
-#pragma unroll
-  for (int k = 0; k <= K; k++) {
-    float wd = nonneg_weight(w, s.T[k]);
-    if (k > 0) wd += irls_l1(w, w.lis, s.T[k]);
-    qv[3 + k] += wd * pc[3 + k];
-  }
-  // E_smoothness (eq:smoothness-term): 4-neighbour stencil per layer.
-#pragma unroll
-  for (int k = 0; k <= K; k++) {
-    const Edges es = smooth_edges(P, P.X, 3 + k, px, s.T[k]);
-    qv[3 + k] += edge_laplace(es, px, pc[3 + k], [&](int dy, int dx) { return pf(3 + k, dy, dx); });
-  }
-}
-
-// Linearisation (fused): g = -J^T F, diag(J^T J); PCG start r = g, z = M^-1 r.
+// Linearisation (fused): g = -J^T F, diag(J^T J); PCG start r = g, z = M^-1 r;
+// the operator coefficients of the step (CoefLayout) in every mode.
 // mode 0: PCG init (writes r, z, Minv, zero delta, rho); mode 1: stage output
-// (writes g to gout and diag to dout).
+// (writes g to gout and diag to dout); mode 2: coefficients only.
 template <int K>
 __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __restrict__ gout,
                                                   float* __restrict__ dout) {
@@ -509,12 +495,15 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
       }
     }
     // E_i-sparsity and E_non-neg.
+    using CL = CoefLayout<K>;
+    float* cf = P.coef + o;
 #pragma unroll
     for (int k = 0; k <= K; k++) {
       float wd = nonneg_weight(w, s.T[k]);
       if (k > 0) wd += irls_l1(w, w.lis, s.T[k]);
       g[3 + k] -= wd * s.T[k];
       dg[3 + k] += wd;
+      cf[(CL::WT + k) * P.plane] = wd;
     }
     // E_smoothness.
 #pragma unroll
@@ -522,7 +511,18 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
       const Edges es = smooth_edges(P, X, 3 + k, px, s.T[k]);
       g[3 + k] -= edge_laplace(es, px, s.T[k], [&](int dy, int dx) { return xf(3 + k, dy, dx); });
       dg[3 + k] += es.R + es.D + es.L + es.U;
+      cf[(CL::ER + k) * P.plane] = es.R;
+      cf[(CL::ED + k) * P.plane] = es.D;
     }
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      cf[(CL::A + c) * P.plane] = w.ld * s.R[c] * s.R[c];
+      cf[(CL::S + c) * P.plane] = s.S[c];
+    }
+    cf[CL::WR * P.plane] = er.R;
+    cf[CL::WD * P.plane] = er.D;
+    cf[CL::DR * P.plane] = w.lcl + (P.temporal ? w.lrc * P.wtsum[o] : 0.f);
+    cf[CL::WM * P.plane] = wm;
     if (mode == 0) {
 #pragma unroll
       for (int v = 0; v < V; v++) {
@@ -535,7 +535,7 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
         P.d[ov] = 0.f;
         rz += g[v] * zz;
       }
-    } else {
+    } else if (mode == 1) {
 #pragma unroll
       for (int v = 0; v < V; v++) {
         const long ov = v * P.plane + o;
@@ -545,7 +545,7 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
     }
   }
   if (mode != 0) return;
-  const double bs = block_sum((double)rz);
+  const double bs = block_sum_f(rz);
   const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
   if (tid_flat() == 0) P.partial[b] = bs;
   if (last_block(&P.sc->cnt[CNT_LIN])) {
@@ -557,105 +557,293 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
   }
 }
 
-// PCG operator step: p = z + beta p_old (first step: p = z), q = J^T J p,
-// <p, q> reduced, alpha = rho / <p, q>.  mode 1 (stage): p = pin, only q.
+// ---------------------------------------------------------------- PCG operator step
+
+// ---- four pixels as two packed FP32 pairs (one packed instruction per pair)
+
+struct F4 {
+  float2 a, b;  // pixels 0,1 and 2,3
+};
+__device__ __forceinline__ F4 f4(float4 v) { return {make_float2(v.x, v.y), make_float2(v.z, v.w)}; }
+__device__ __forceinline__ F4 f4s(float s) { return {make_float2(s, s), make_float2(s, s)}; }
+__device__ __forceinline__ F4 f4v(float x, float y, float z, float w) { return {make_float2(x, y), make_float2(z, w)}; }
+__device__ __forceinline__ float4 to4(F4 v) { return make_float4(v.a.x, v.a.y, v.b.x, v.b.y); }
+__device__ __forceinline__ F4 fma4(F4 x, F4 y, F4 z) { return {__ffma2_rn(x.a, y.a, z.a), __ffma2_rn(x.b, y.b, z.b)}; }
+__device__ __forceinline__ F4 mul4(F4 x, F4 y) { return {__fmul2_rn(x.a, y.a), __fmul2_rn(x.b, y.b)}; }
+__device__ __forceinline__ F4 add4(F4 x, F4 y) { return {__fadd2_rn(x.a, y.a), __fadd2_rn(x.b, y.b)}; }
+// x - y, exactly rounded (one fused multiply-add by -1)
+__device__ __forceinline__ F4 sub4(F4 x, F4 y) {
+  const float2 m = make_float2(-1.f, -1.f);
+  return {__ffma2_rn(y.a, m, x.a), __ffma2_rn(y.b, m, x.b)};
+}
+__device__ __forceinline__ float dot4(F4 x, F4 y) {
+  const float2 t = __ffma2_rn(x.b, y.b, __fmul2_rn(x.a, y.a));
+  return t.x + t.y;
+}
+__device__ __forceinline__ F4 ldg4(const float* p) { return f4(*reinterpret_cast<const float4*>(p)); }
+__device__ __forceinline__ F4 lds4(const float* p) { return f4(*reinterpret_cast<const float4*>(p)); }
+
+// Tile of the operator kernel: 128 x 8 pixels per 32 x 8 block, four
+// consecutive pixels in x per thread.  p = z + beta p_old is formed once per
+// position into shared memory in aligned float4 chunks: rows y0-3 .. y0+10 of
+// the reflectance channels (the consistency pairs reach 3 pixels) and rows
+// y0-1 .. y0+8 of the layers, columns x0-4 .. x0+131 (halo padded to a float4).
+constexpr int QW = 4, VTW = BX * QW, VHX = 4, VRW = VHX + VTW + 4, AHR = 3;
+
 template <int K>
-__global__ void __launch_bounds__(NT) k_apply(Params P, int mode, int first, const float* __restrict__ pin,
-                                              float* __restrict__ pout, float* __restrict__ qout) {
-  constexpr int V = K + 4;
+struct ApplyTile {
+  float pr[3][BY + 2 * AHR][VRW];
+  float pt[K + 1][BY + 2][VRW];
+};
+
+// PCG operator step: p = z + beta p_old (first step: p = z), q = J^T J p from
+// the step's coefficient planes, <p, q> reduced, alpha = rho / <p, q>.  The
+// stencil is applied to z only: q = J^T J z + beta q_old equals J^T J p since
+// J^T J is fixed within a Gauss-Newton step, so only z needs a halo and p_old,
+// q_old are read at the thread's own pixels (p and q may be updated in place).
+// mode 1 (stage): q = J^T J pin.  Padding columns (W <= x < pitch) of p, q, z
+// and of every coefficient plane are zero and stay zero.
+template <int K>
+__global__ void __launch_bounds__(NT, 2) k_apply(Params P, int mode, int first, const float* pin, float* pout,
+                                                 float* __restrict__ qout) {
+  using CL = CoefLayout<K>;
+  constexpr int NCH = VRW / 4;  // float4 chunks per staged row
+  extern __shared__ float4 apply_smem[];
+  ApplyTile<K>& t = *reinterpret_cast<ApplyTile<K>*>(apply_smem);
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
+  const Weights& w = P.w;
   const float beta = (mode == 0 && !first) ? (float)P.sc->beta : 0.f;
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  const int x0 = blockIdx.x * VTW, y0 = blockIdx.y * BY, tid = tid_flat();
+  // Stage s = z (PCG step) or s = pin (stage call) with its halo.  Each thread
+  // issues up to SB chunk loads before storing any, so a block needs only a
+  // couple of memory round trips.
+  const float* __restrict__ sv = mode == 0 ? P.z : pin;
+  constexpr int NR = 3 * (BY + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (BY + 2) * NCH, SB = 8;
+  auto chunk_dst = [&](int i, int& gy, int& gx, int& v) -> float* {
+    if (i < NR) {
+      const int c = i / ((BY + 2 * AHR) * NCH), rem = i - c * (BY + 2 * AHR) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
+      gy = y0 - AHR + ly;
+      gx = x0 - VHX + 4 * lc;
+      v = c;
+      return &t.pr[c][ly][4 * lc];
+    }
+    const int j = i - NR, k = j / ((BY + 2) * NCH), rem = j - k * (BY + 2) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
+    gy = y0 - 1 + ly;
+    gx = x0 - VHX + 4 * lc;
+    v = 3 + k;
+    return &t.pt[k][ly][4 * lc];
+  };
+  for (int base = tid; base < NTOT; base += SB * NT) {
+    float4 val[SB];
+#pragma unroll
+    for (int s = 0; s < SB; s++) {
+      const int i = base + s * NT;
+      val[s] = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (i < NTOT) {
+        int gy, gx, v;
+        chunk_dst(i, gy, gx, v);
+        if (gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch)
+          val[s] = *reinterpret_cast<const float4*>(sv + v * P.plane + off2(P, gy, gx));
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < SB; s++) {
+      const int i = base + s * NT;
+      if (i < NTOT) {
+        int gy, gx, v;
+        *reinterpret_cast<float4*>(chunk_dst(i, gy, gx, v)) = val[s];
+      }
+    }
+  }
+  __syncthreads();
   float pq = 0.f;
+  const int y = y0 + threadIdx.y, x = x0 + QW * threadIdx.x;
   if (x < P.W && y < P.H) {
-    const Pix px = make_pix(P, x, y);
     const long o = off2(P, y, x);
-    const float* __restrict__ z = P.z;
-    auto pf = [&](int v, int dy, int dx) -> float {
-      const long a = v * P.plane + o + (long)dy * P.pitch + dx;
-      if (mode != 0) return pin[a];
-      return first ? z[a] : fmaf(beta, pin[a], z[a]);
+    const float* __restrict__ cf = P.coef + o;
+    const long PL = P.plane;
+    const bool hL = x > 0, hU = y > 0;
+    const F4 valid = f4v(1.f, x + 1 < P.W ? 1.f : 0.f, x + 2 < P.W ? 1.f : 0.f, x + 3 < P.W ? 1.f : 0.f);
+    // q = A s on the valid pixels; in a PCG step p = z + beta p_old and, A being
+    // fixed within the Gauss-Newton step, q = A p = A z + beta q_old.
+    const F4 bb = f4s(beta);
+    auto finish = [&](int v, F4 s, F4 as) {
+      F4 q = mul4(as, valid), p = s;
+      const long ov = v * PL + o;
+      if (mode == 0 && !first) {
+        p = fma4(bb, ldg4(pin + ov), s);
+        q = fma4(bb, ldg4(qout + ov), q);
+      }
+      *reinterpret_cast<float4*>(qout + ov) = to4(q);
+      if (mode == 0) *reinterpret_cast<float4*>(pout + ov) = to4(p);
+      pq += dot4(p, q);
     };
-    PixState<K> s;
-    load_state<K>(P, ct, o, s);
-    float pc[V], qv[V];
+    const int cx = VHX + QW * threadIdx.x, ry = threadIdx.y + AHR, ty = threadIdx.y + 1;
+    // data and monochrome blocks: P_c = sum_k b_kc p_Tk, M_c = sum_k dm_kc p_Tk
+    F4 Pc[3], Mc[3];
 #pragma unroll
-    for (int v = 0; v < V; v++) pc[v] = pf(v, 0, 0);
-    normal_apply<K>(P, ct, px, o, s, pc, pf, qv);
+    for (int c = 0; c < 3; c++) Pc[c] = Mc[c] = f4s(0.f);
 #pragma unroll
-    for (int v = 0; v < V; v++) {
-      const long ov = v * P.plane + o;
-      qout[ov] = qv[v];
-      if (mode == 0) pout[ov] = pc[v];
-      pq += pc[v] * qv[v];
+    for (int k = 0; k <= K; k++) {
+      const F4 pk = lds4(&t.pt[k][ty][cx]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        Pc[c] = fma4(f4s(ct.b[k][c]), pk, Pc[c]);
+        Mc[c] = fma4(f4s(ct.dm[k][c]), pk, Mc[c]);
+      }
+    }
+    const F4 wm = ldg4(cf + CL::WM * PL), dr = ldg4(cf + CL::DR * PL);
+    F4 u[3];
+    // reflectance channels: data, clustering/temporal diagonal, r-sparsity, consistency
+    const F4 eR = ldg4(cf + CL::WR * PL), eD = ldg4(cf + CL::WD * PL);
+    const float eLm = hL ? cf[CL::WR * PL - 1] : 0.f;
+    const F4 eL = f4v(eLm, eR.a.x, eR.a.y, eR.b.x);
+    const F4 eU = hU ? ldg4(cf + CL::WD * PL - P.pitch) : f4s(0.f);
+    F4 qr[3], pcr[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const F4 Sc = ldg4(cf + (CL::S + c) * PL), Ac = ldg4(cf + (CL::A + c) * PL);
+      const float* row = &t.pr[c][ry][cx];
+      const F4 pc = lds4(row);
+      pcr[c] = pc;
+      u[c] = mul4(Ac, fma4(Sc, pc, Pc[c]));
+      const F4 right = f4v(pc.a.y, pc.b.x, pc.b.y, row[4]);
+      const F4 left = f4v(row[-1], pc.a.x, pc.a.y, pc.b.x);
+      const F4 down = lds4(&t.pr[c][ry + 1][cx]), up = lds4(&t.pr[c][ry - 1][cx]);
+      F4 q = fma4(Sc, u[c], mul4(dr, pc));
+      q = fma4(eR, sub4(pc, right), q);
+      q = fma4(eL, sub4(pc, left), q);
+      q = fma4(eD, sub4(pc, down), q);
+      qr[c] = fma4(eU, sub4(pc, up), q);
+    }
+    // consistency pairs (x, x + o_j) and (x - o_j, x), weights of this group and of the partners
+    for (int j = 0; j < P.ns; j++) {
+      const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
+      const F4 of = mul4(f4s(w.lrc), ldg4(P.ws + j * PL + o));
+      float bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; i++)
+        bv[i] = inside(P, y - dy, x + i - dx) ? w.lrc * P.ws[j * PL + o + i - (long)dy * P.pitch - dx] : 0.f;
+      const F4 ob = f4v(bv[0], bv[1], bv[2], bv[3]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float* fw = &t.pr[c][ry + dy][cx + dx];
+        const float* bw = &t.pr[c][ry - dy][cx - dx];
+        qr[c] = fma4(of, sub4(pcr[c], f4v(fw[0], fw[1], fw[2], fw[3])), qr[c]);
+        qr[c] = fma4(ob, sub4(pcr[c], f4v(bw[0], bw[1], bw[2], bw[3])), qr[c]);
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 3; c++) finish(c, pcr[c], qr[c]);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
+    // layers: data and monochrome back-projections, diagonal IRLS weights, smoothness
+#pragma unroll
+    for (int k = 0; k <= K; k++) {
+      const float* row = &t.pt[k][ty][cx];
+      const F4 pk = lds4(row);
+      const F4 sR = ldg4(cf + (CL::ER + k) * PL), sD = ldg4(cf + (CL::ED + k) * PL);
+      const float sLm = hL ? cf[(CL::ER + k) * PL - 1] : 0.f;
+      const F4 sL = f4v(sLm, sR.a.x, sR.a.y, sR.b.x);
+      const F4 sU = hU ? ldg4(cf + (CL::ED + k) * PL - P.pitch) : f4s(0.f);
+      const F4 right = f4v(pk.a.y, pk.b.x, pk.b.y, row[4]);
+      const F4 left = f4v(row[-1], pk.a.x, pk.a.y, pk.b.x);
+      const F4 down = lds4(&t.pt[k][ty + 1][cx]), up = lds4(&t.pt[k][ty - 1][cx]);
+      F4 q = mul4(ldg4(cf + (CL::WT + k) * PL), pk);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        q = fma4(f4s(ct.b[k][c]), u[c], q);
+        q = fma4(f4s(ct.dm[k][c]), Mc[c], q);
+      }
+      q = fma4(sR, sub4(pk, right), q);
+      q = fma4(sL, sub4(pk, left), q);
+      q = fma4(sD, sub4(pk, down), q);
+      q = fma4(sU, sub4(pk, up), q);
+      finish(3 + k, pk, q);
     }
   }
   if (mode != 0) return;
-  const double bs = block_sum((double)pq);
+  const double bs = block_sum_f(pq);
   const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tid_flat() == 0) P.partial[b] = bs;
+  if (tid == 0) P.partial[b] = bs;
   if (last_block(&P.sc->cnt[CNT_APPLY])) {
-    const double t = grid_total(P.partial, nb, 1, 0);
-    if (tid_flat() == 0) {
-      P.sc->pq = t;
-      P.sc->alpha = t != 0.0 ? P.sc->rho / t : 0.0;
+    const double tt = grid_total(P.partial, nb, 1, 0);
+    if (tid == 0) {
+      P.sc->pq = tt;
+      P.sc->alpha = tt != 0.0 ? P.sc->rho / tt : 0.0;
     }
   }
 }
 
-// PCG vector step: delta += alpha p, r -= alpha q, z = M^-1 r, rho' = <r, z>,
-// beta = rho' / rho.  last 1: X += delta + alpha p (the Gauss-Newton update);
-// last 2: write delta only.
+// ---------------------------------------------------------------- PCG vector step
+
+// delta += alpha p, r -= alpha q, z = M^-1 r, rho' = <r, z>, beta = rho' / rho.
+// last 1: X += delta + alpha p (the Gauss-Newton update); last 2: write delta
+// only.  Works on whole pitched planes as float4 (the padding columns of every
+// PCG vector are zero and stay zero).  Grid (plane / 4 / 256, V): one float4
+// of one plane per thread, for enough independent loads in flight.
 template <int K>
-__global__ void __launch_bounds__(NT) k_update(Params P, const float* __restrict__ p, int last) {
-  constexpr int V = K + 4;
+__global__ void __launch_bounds__(256) k_update(Params P, const float* __restrict__ p, int last) {
   const float alpha = (float)P.sc->alpha;
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  const long n4 = P.plane >> 2;
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long o = (long)blockIdx.y * n4 + i;
+  const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
+  float4* __restrict__ d4 = reinterpret_cast<float4*>(P.d);
   float rz = 0.f;
-  if (x < P.W && y < P.H) {
-    const long o = off2(P, y, x);
-#pragma unroll
-    for (int v = 0; v < V; v++) {
-      const long ov = v * P.plane + o;
-      const float dn = fmaf(alpha, p[ov], P.d[ov]);
-      if (last == 1) {
-        P.X[ov] += dn;
-      } else if (last == 2) {
-        P.d[ov] = dn;
-      } else {
-        P.d[ov] = dn;
-        const float rn = fmaf(-alpha, P.q[ov], P.r[ov]);
-        const float zz = P.Minv[ov] * rn;
-        P.r[ov] = rn;
-        P.z[ov] = zz;
-        rz += rn * zz;
-      }
+  auto axpy = [](float a, float4 x, float4 y) {
+    return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
+  };
+  if (i < n4) {
+    if (last == 1) {
+      float4* __restrict__ X4 = reinterpret_cast<float4*>(P.X);
+      const float4 dn = axpy(alpha, p4[o], d4[o]);
+      const float4 xv = X4[o];
+      X4[o] = make_float4(xv.x + dn.x, xv.y + dn.y, xv.z + dn.z, xv.w + dn.w);
+    } else if (last == 2) {
+      d4[o] = axpy(alpha, p4[o], d4[o]);
+    } else {
+      const float4 pv = p4[o], dv = d4[o];
+      const float4 qv = reinterpret_cast<const float4*>(P.q)[o];
+      const float4 rv = reinterpret_cast<const float4*>(P.r)[o];
+      const float4 mv = reinterpret_cast<const float4*>(P.Minv)[o];
+      d4[o] = axpy(alpha, pv, dv);
+      const float4 rn = axpy(-alpha, qv, rv);
+      const float4 zz = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
+      reinterpret_cast<float4*>(P.r)[o] = rn;
+      reinterpret_cast<float4*>(P.z)[o] = zz;
+      rz = rn.x * zz.x + rn.y * zz.y + rn.z * zz.z + rn.w * zz.w;
     }
   }
   if (last) return;
-  const double bs = block_sum((double)rz);
+  const double bs = block_sum_f(rz);
   const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tid_flat() == 0) P.partial[b] = bs;
+  if (threadIdx.x == 0) P.partial[b] = bs;
   if (last_block(&P.sc->cnt[CNT_UPDATE])) {
-    const double t = grid_total(P.partial, nb, 1, 0);
-    if (tid_flat() == 0) {
+    const double tt = grid_total(P.partial, nb, 1, 0);
+    if (threadIdx.x == 0) {
       const double rho = P.sc->rho;
-      P.sc->beta = rho != 0.0 ? t / rho : 0.0;
-      P.sc->rho = t;
+      P.sc->beta = rho != 0.0 ? tt / rho : 0.0;
+      P.sc->rho = tt;
     }
   }
 }
+
+// ---------------------------------------------------------------- base-colour step
 
 // Base-colour refinement (eq:basecolorrefinement): per channel c the K x K
 // normal matrix A_c = l_data sum_x R_c^2 T_k T_l + (l_IR + l_CR) I and
 // g_c = l_data sum_x R_c T_k e_c, e_c the data residual at the initial colours;
 // the last block solves the three SPD systems by FP64 Cholesky and sets
-// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel.
+// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel; 256 threads.
+// Partials: (K (K + 1) / 2 + K) values x (3 nblk) blocks doubles, value-major.
 template <int K>
 __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
-  constexpr int NA = K * (K + 1) / 2, NACC = NA + K;
+  constexpr int NA = K * (K + 1) / 2, NACC = NA + K, NW = 8;
   __shared__ ColorTable<K> ct;
+  __shared__ double wsum[NW][NACC];
+  __shared__ double tot[3][NACC];
   load_colors<K>(ct, P.col);
   const int c = blockIdx.y;
   const long HW = (long)P.H * P.W;
@@ -685,66 +873,91 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
 #pragma unroll
     for (int k = 0; k < K; k++) acc[NA + k] += a[k] * e;
   }
-  const int b = blockIdx.y * gridDim.x + blockIdx.x;
+  // block reduction: FP64 warp shuffles, then the 8 warp sums in order
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
   for (int i = 0; i < NACC; i++) {
-    const double s = block_sum((double)acc[i]);
-    if (threadIdx.x == 0) P.partial[(long)b * NACC + i] = s;
+    float v = acc[i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if (lane == 0) wsum[wid][i] = (double)v;
+  }
+  __syncthreads();
+  const int nbt = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+  if (threadIdx.x < NACC) {
+    double s = 0.0;
+    for (int ww = 0; ww < NW; ww++) s += wsum[ww][threadIdx.x];
+    P.partial[(long)threadIdx.x * nbt + b] = s;
   }
   if (!last_block(&P.sc->cnt[CNT_DENSE])) return;
-  __shared__ double tot[3][NACC];
-  for (int cc = 0; cc < 3; cc++)
-    for (int i = 0; i < NACC; i++) {
-      double s = 0.0;
-      for (int bb = threadIdx.x; bb < (int)gridDim.x; bb += blockDim.x)
-        s += __ldcg(P.partial + (long)(cc * gridDim.x + bb) * NACC + i);
-      s = block_sum(s);
-      if (threadIdx.x == 0) tot[cc][i] = s;
-    }
+  // each warp sums whole (channel, value) rows: lanes stride the blocks, then a shuffle tree
+  for (int row = wid; row < 3 * NACC; row += NW) {
+    const int cc = row / NACC, i = row - cc * NACC;
+    const double* src = P.partial + (long)i * nbt + (long)cc * gridDim.x;
+    double s = 0.0;
+    for (int bb = lane; bb < (int)gridDim.x; bb += 32) s += __ldcg(src + bb);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (lane == 0) tot[cc][i] = s;
+  }
   __syncthreads();
   if (threadIdx.x < 3) {
     const int cc = threadIdx.x;
     const double ld = P.w.ld, ridge = (double)P.w.lIR + (double)P.w.lCR;
     double A[K][K], L[K][K], g[K], yv[K], xs[K];
     int n = 0;
+#pragma unroll
     for (int k = 0; k < K; k++)
+#pragma unroll
       for (int l = 0; l <= k; l++) {
         A[k][l] = A[l][k] = ld * tot[cc][n++];
       }
+#pragma unroll
     for (int k = 0; k < K; k++) {
       A[k][k] += ridge;
       g[k] = ld * tot[cc][NA + k];
     }
+#pragma unroll
     for (int k = 0; k < K; k++) {
       P.sc->g[cc * K + k] = g[k];
+#pragma unroll
       for (int l = 0; l < K; l++) P.sc->A[(cc * K + k) * K + l] = A[k][l];
     }
     if (solve) {
       bool ok = true;
-      for (int j = 0; j < K && ok; j++) {
+      double rd[K];  // 1 / L_jj
+#pragma unroll
+      for (int j = 0; j < K; j++) {
         double s = A[j][j];
+#pragma unroll
         for (int m = 0; m < j; m++) s -= L[j][m] * L[j][m];
-        if (!(s > 0.0)) {
-          ok = false;
-          break;
-        }
-        L[j][j] = sqrt(s);
+        ok = ok && (s > 0.0);
+        L[j][j] = sqrt(s > 0.0 ? s : 1.0);
+        rd[j] = 1.0 / L[j][j];
+#pragma unroll
         for (int i = j + 1; i < K; i++) {
-          double t = A[i][j];
-          for (int m = 0; m < j; m++) t -= L[i][m] * L[j][m];
-          L[i][j] = t / L[j][j];
+          double tt = A[i][j];
+#pragma unroll
+          for (int m = 0; m < j; m++) tt -= L[i][m] * L[j][m];
+          L[i][j] = tt * rd[j];
         }
       }
       if (ok) {
+#pragma unroll
         for (int i = 0; i < K; i++) {
-          double t = g[i];
-          for (int m = 0; m < i; m++) t -= L[i][m] * yv[m];
-          yv[i] = t / L[i][i];
+          double tt = g[i];
+#pragma unroll
+          for (int m = 0; m < i; m++) tt -= L[i][m] * yv[m];
+          yv[i] = tt * rd[i];
         }
+#pragma unroll
         for (int i = K - 1; i >= 0; i--) {
-          double t = yv[i];
-          for (int m = i + 1; m < K; m++) t -= L[m][i] * xs[m];
-          xs[i] = t / L[i][i];
+          double tt = yv[i];
+#pragma unroll
+          for (int m = i + 1; m < K; m++) tt -= L[m][i] * xs[m];
+          xs[i] = tt * rd[i];
         }
+#pragma unroll
         for (int k = 0; k < K; k++) {
           const double bn = (double)P.col->binit[k * 3 + cc] + xs[k];
           P.col->bd[k * 3 + cc] = bn;
@@ -826,7 +1039,7 @@ __global__ void __launch_bounds__(NT) k_energy(Params P) {
   }
   const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
   for (int i = 0; i < 8; i++) {
-    const double s = block_sum((double)E[i]);
+    const double s = block_sum_f(E[i]);
     if (tid_flat() == 0) P.partial[(long)b * 8 + i] = s;
   }
   if (last_block(&P.sc->cnt[CNT_ENERGY]))
