@@ -247,6 +247,8 @@ def run_gid(args, ws, rank, local):
             s.init(0 if t == 0 else 1)
             s.run(N, M)
 
+    step()
+    tile_rows, tile_us = s.autotune(10)     # operator tile shape for this frame size (setup, untimed)
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -332,7 +334,8 @@ def run_gid(args, ws, rank, local):
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": WORKLOAD, "H": H, "W": W, "K": K, "frames_per_step": F, "N_outer": N,
                           "M_inner": M, "l2": "flushed before each step (256 MB write, outside the events)",
-                          "parallelism": f"replicas x{ws} (one video per GPU)"},
+                          "parallelism": f"replicas x{ws} (one video per GPU)",
+                          "operator_tile": f"128x{tile_rows} (autotuned; us per PCG step {tile_us})"},
                "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
                "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E}
         print(json.dumps(out), flush=True)

@@ -168,6 +168,21 @@ int gid_stage_pcg(gid_ctx* ctx, int m_inner, float* delta_dev);
  * Synchronises. */
 int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 
+/* ---- operator tile shape ---- */
+
+/* Rows per tile of the PCG operator kernel: 2, 4 (default), 8 or 17 (128 pixels
+ * wide each; 17 runs one 544-thread block per SM).  Results do not depend on
+ * it; only speed does. */
+int gid_set_apply_tile(gid_ctx* ctx, int rows);
+
+/* Time reps PCG steps (operator + vector step) with each operator tile shape
+ * on the current frame and state (CUDA events on the context stream) and keep
+ * the fastest.  Writes the chosen rows to *rows_out and the four timings (us
+ * per PCG step, shapes 2, 4, 8, 17) to us_out[4]; either may be NULL.  Needs
+ * gid_set_frame and a state; leaves the state X unchanged (the PCG vectors are
+ * scratch until the next gid_run).  Call it between runs.  Synchronises. */
+int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
+
 /* ---- instrumentation ---- */
 
 /* Kernel kinds for gid_profile_read. */

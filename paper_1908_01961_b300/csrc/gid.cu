@@ -37,6 +37,7 @@ struct gid_ctx {
   bool has_colors = false, has_frame = false, initialised = false, temporal_active = false;
   int frames_solved = 0;
   long long launches = 0;  // kernels launched by this context
+  int apply_th = 4;        // rows per operator tile (gid_set_apply_tile / gid_autotune)
   // optional per-kernel CUDA-event timing (gid_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -150,15 +151,24 @@ struct Launch {
   static void linearize(const gid_ctx* c, int mode, float* g, float* dg) {
     k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg);
   }
-  static void apply(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
+  template <int TH>
+  static void apply_th(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
     static bool attr = false;  // opt in to > 48 KB of dynamic shared memory once per instantiation
-    const size_t smem = sizeof(ApplyTile<K>);
+    const size_t smem = sizeof(ApplyTile<K, TH>);
     if (!attr) {
-      cudaFuncSetAttribute(k_apply<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(k_apply<K, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
       attr = true;
     }
-    const dim3 grid((c->W + VTW - 1) / VTW, (c->H + BY - 1) / BY);
-    k_apply<K><<<grid, dim3(BX, BY), smem, c->stream>>>(params(c), mode, first, pin, pout, qout);
+    const dim3 grid((c->W + VTW - 1) / VTW, (c->H + TH - 1) / TH);
+    k_apply<K, TH><<<grid, dim3(BX, TH), smem, c->stream>>>(params(c), mode, first, pin, pout, qout);
+  }
+  static void apply(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
+    switch (c->apply_th) {
+      case 2: apply_th<2>(c, mode, first, pin, pout, qout); break;
+      case 4: apply_th<4>(c, mode, first, pin, pout, qout); break;
+      case 17: apply_th<17>(c, mode, first, pin, pout, qout); break;
+      default: apply_th<8>(c, mode, first, pin, pout, qout); break;
+    }
   }
   static void update(const gid_ctx* c, const float* p, int last) {
     const long n4 = c->plane / 4;
@@ -273,10 +283,10 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->plane = (long)H * c->pitch;
   const int ns = std::max(1, w->n_spatial_pairs), nt = std::max(1, w->n_temporal_pairs);
   // planes: I 3, C 3, Cprev 3, rprev 3, wsr 1, ws ns, wt nt, wtsum 1, X d r z pA pB q Minv 8V, coefficients
-  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V + coef_planes(K);
+  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V + coef_planes(K, w->n_spatial_pairs);
   const size_t fbytes = (size_t)nplanes * c->plane * sizeof(float) + 256 * (size_t)nplanes;
   const size_t lbytes = ((size_t)c->plane + 255) / 256 * 256;
-  const long nb = (long)pix_grid(c).x * pix_grid(c).y;
+  const long nb = std::max((long)pix_grid(c).x * pix_grid(c).y, (long)((W + VTW - 1) / VTW) * ((H + 1) / 2));
   const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
   const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
   const size_t pbytes = (size_t)npart * sizeof(double);
@@ -309,7 +319,7 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->pB = planes(c->V);
   c->q = planes(c->V);
   c->Minv = planes(c->V);
-  c->coef = planes(coef_planes(K));
+  c->coef = planes(coef_planes(K, w->n_spatial_pairs));
   c->lab = (uint8_t*)take(lbytes);
   c->col = (DevColors*)take(sizeof(DevColors));
   c->sc = (DevScalars*)take(sizeof(DevScalars));
@@ -621,5 +631,60 @@ extern "C" int gid_profile_read(gid_ctx* c, double* ms, long long* count) {
     c->prof_ms[k] = 0;
     c->prof_n[k] = 0;
   }
+  return GID_OK;
+}
+
+// ---------------------------------------------------------------- operator tile shape
+
+extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (rows != 2 && rows != 4 && rows != 8 && rows != 17)
+    return fail(c, GID_ERR_INVALID_ARG, "tile rows must be 2, 4, 8 or 17");
+  c->apply_th = rows;
+  return GID_OK;
+}
+
+extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) {
+  if (!c || reps < 1) return fail(c, GID_ERR_INVALID_ARG, "bad argument");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "autotune needs a frame and a state");
+  // A PCG start at the current state, then timed (operator step + vector step)
+  // pairs: the in-loop cost, cache interference included.  The PCG vectors and
+  // scalars it touches are re-initialised by the next Gauss-Newton step; X is
+  // not modified.
+  launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
+  if (int rc = check_launch(c, "k_linearize")) return rc;
+  cudaEvent_t e0, e1;
+  GID_TRY_CUDA(c, cudaEventCreate(&e0));
+  GID_TRY_CUDA(c, cudaEventCreate(&e1));
+  const int cand[4] = {2, 4, 8, 17};
+  float best = 1e30f;
+  int best_th = c->apply_th;
+  for (int i = 0; i < 4; i++) {
+    c->apply_th = cand[i];
+    auto pair = [&](int first) {
+      GID_DISPATCH(c, apply, c, 0, first, (const float*)c->pA, c->pA, c->q);
+      GID_DISPATCH(c, update, c, (const float*)c->pA, 0);
+    };
+    pair(1);
+    pair(0);
+    cudaEventRecord(e0, c->stream);
+    for (int r = 0; r < reps; r++) pair(0);
+    cudaEventRecord(e1, c->stream);
+    c->launches += 2 * (reps + 2);
+    if (int rc = check_launch(c, "k_apply")) return rc;
+    GID_TRY_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GID_TRY_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    const float us = 1000.f * ms / reps;
+    if (us_out) us_out[i] = us;
+    if (us < best) {
+      best = us;
+      best_th = cand[i];
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->apply_th = best_th;
+  if (rows_out) *rows_out = best_th;
   return GID_OK;
 }

@@ -209,12 +209,14 @@ __device__ __forceinline__ void load_colors(ColorTable<K>& t, const DevColors* c
 //   WT (K+1)   non-negativity + decomposition-sparsity diagonal of each layer
 //   DR         lambda_clustering + temporal consistency diagonal of r
 //   WM         lambda_monochrome w_SR
+//   CW + j     lambda_r-consistency omega_j(x): pair (x, x + o_j), 0 if x + o_j is outside
+//   CW + ns + j  lambda_r-consistency omega_j(x - o_j): pair (x - o_j, x), 0 if x - o_j is outside
 template <int K>
 struct CoefLayout {
   static constexpr int A = 0, S = 3, WR = 6, WD = 7, ER = 8, ED = 8 + (K + 1), WT = 8 + 2 * (K + 1),
-                       DR = 8 + 3 * (K + 1), WM = 9 + 3 * (K + 1), N = 10 + 3 * (K + 1);
+                       DR = 8 + 3 * (K + 1), WM = 9 + 3 * (K + 1), CW = 10 + 3 * (K + 1);
 };
-constexpr int coef_planes(int K) { return 10 + 3 * (K + 1); }
+constexpr int coef_planes(int K, int ns) { return 10 + 3 * (K + 1) + 2 * ns; }
 
 // ---------------------------------------------------------------- stencil helpers
 
@@ -454,20 +456,23 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
     // E_r-consistency, spatial.
     for (int j = 0; j < P.ns; j++) {
       const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
+      float of = 0.f, ob = 0.f;
       if (inside(P, y + dy, x + dx)) {
-        const float of = w.lrc * P.ws[j * P.plane + o];
+        of = w.lrc * P.ws[j * P.plane + o];
         for (int c = 0; c < 3; c++) {
           g[c] -= of * (s.rr[c] - xf(c, dy, dx));
           dg[c] += of;
         }
       }
       if (inside(P, y - dy, x - dx)) {
-        const float ob = w.lrc * P.ws[j * P.plane + o - (long)dy * P.pitch - dx];
+        ob = w.lrc * P.ws[j * P.plane + o - (long)dy * P.pitch - dx];
         for (int c = 0; c < 3; c++) {
           g[c] -= ob * (s.rr[c] - xf(c, -dy, -dx));
           dg[c] += ob;
         }
       }
+      P.coef[(CoefLayout<K>::CW + j) * P.plane + o] = of;
+      P.coef[(CoefLayout<K>::CW + P.ns + j) * P.plane + o] = ob;
     }
     // E_r-consistency, temporal: residual r(x) - r_prev(x + o_j).
     if (P.temporal) {
@@ -590,10 +595,34 @@ __device__ __forceinline__ F4 lds4(const float* p) { return f4(*reinterpret_cast
 // y0-1 .. y0+8 of the layers, columns x0-4 .. x0+131 (halo padded to a float4).
 constexpr int QW = 4, VTW = BX * QW, VHX = 4, VRW = VHX + VTW + 4, AHR = 3;
 
-template <int K>
+template <int K, int TH>
 struct ApplyTile {
-  float pr[3][BY + 2 * AHR][VRW];
-  float pt[K + 1][BY + 2][VRW];
+  float pr[3][TH + 2 * AHR][VRW];
+  float pt[K + 1][TH + 2][VRW];
+};
+
+// Apply tile shapes: TH rows of 128 pixels, a 32 x TH block, at most MAXREG
+// registers per thread (MINB blocks of it fit in one SM's register file).
+template <int TH>
+struct ApplyShape;
+template <>
+struct ApplyShape<8> {
+  static constexpr int MINB = 2, MAXREG = 128;
+};
+template <>
+struct ApplyShape<4> {
+  static constexpr int MINB = 4, MAXREG = 128;
+};
+template <>
+struct ApplyShape<2> {
+  static constexpr int MINB = 8, MAXREG = 128;
+};
+// 17 rows, one 544-thread block per SM: a 640 x 480 frame is 145 such tiles,
+// one wave on 148 SMs.  17 warps put 5 warps on one SM sub-partition (16 K
+// registers), hence at most 96 registers per thread.
+template <>
+struct ApplyShape<17> {
+  static constexpr int MINB = 1, MAXREG = 96;
 };
 
 // PCG operator step: p = z + beta p_old (first step: p = z), q = J^T J p from
@@ -603,42 +632,42 @@ struct ApplyTile {
 // q_old are read at the thread's own pixels (p and q may be updated in place).
 // mode 1 (stage): q = J^T J pin.  Padding columns (W <= x < pitch) of p, q, z
 // and of every coefficient plane are zero and stay zero.
-template <int K>
-__global__ void __launch_bounds__(NT, 2) k_apply(Params P, int mode, int first, const float* pin, float* pout,
-                                                 float* __restrict__ qout) {
+template <int K, int TH>
+__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
+    k_apply(Params P, int mode, int first, const float* pin, float* pout, float* __restrict__ qout) {
   using CL = CoefLayout<K>;
   constexpr int NCH = VRW / 4;  // float4 chunks per staged row
+  constexpr int NTH = BX * TH;  // threads per block
   extern __shared__ float4 apply_smem[];
-  ApplyTile<K>& t = *reinterpret_cast<ApplyTile<K>*>(apply_smem);
+  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
-  const Weights& w = P.w;
   const float beta = (mode == 0 && !first) ? (float)P.sc->beta : 0.f;
-  const int x0 = blockIdx.x * VTW, y0 = blockIdx.y * BY, tid = tid_flat();
+  const int x0 = blockIdx.x * VTW, y0 = blockIdx.y * TH, tid = tid_flat();
   // Stage s = z (PCG step) or s = pin (stage call) with its halo.  Each thread
   // issues up to SB chunk loads before storing any, so a block needs only a
   // couple of memory round trips.
   const float* __restrict__ sv = mode == 0 ? P.z : pin;
-  constexpr int NR = 3 * (BY + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (BY + 2) * NCH, SB = 8;
+  constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH, SB = 8;
   auto chunk_dst = [&](int i, int& gy, int& gx, int& v) -> float* {
     if (i < NR) {
-      const int c = i / ((BY + 2 * AHR) * NCH), rem = i - c * (BY + 2 * AHR) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
+      const int c = i / ((TH + 2 * AHR) * NCH), rem = i - c * (TH + 2 * AHR) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
       gy = y0 - AHR + ly;
       gx = x0 - VHX + 4 * lc;
       v = c;
       return &t.pr[c][ly][4 * lc];
     }
-    const int j = i - NR, k = j / ((BY + 2) * NCH), rem = j - k * (BY + 2) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
+    const int j = i - NR, k = j / ((TH + 2) * NCH), rem = j - k * (TH + 2) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
     gy = y0 - 1 + ly;
     gx = x0 - VHX + 4 * lc;
     v = 3 + k;
     return &t.pt[k][ly][4 * lc];
   };
-  for (int base = tid; base < NTOT; base += SB * NT) {
+  for (int base = tid; base < NTOT; base += SB * NTH) {
     float4 val[SB];
 #pragma unroll
     for (int s = 0; s < SB; s++) {
-      const int i = base + s * NT;
+      const int i = base + s * NTH;
       val[s] = make_float4(0.f, 0.f, 0.f, 0.f);
       if (i < NTOT) {
         int gy, gx, v;
@@ -649,7 +678,7 @@ __global__ void __launch_bounds__(NT, 2) k_apply(Params P, int mode, int first, 
     }
 #pragma unroll
     for (int s = 0; s < SB; s++) {
-      const int i = base + s * NT;
+      const int i = base + s * NTH;
       if (i < NTOT) {
         int gy, gx, v;
         *reinterpret_cast<float4*>(chunk_dst(i, gy, gx, v)) = val[s];
@@ -717,21 +746,19 @@ __global__ void __launch_bounds__(NT, 2) k_apply(Params P, int mode, int first, 
       q = fma4(eD, sub4(pc, down), q);
       qr[c] = fma4(eU, sub4(pc, up), q);
     }
-    // consistency pairs (x, x + o_j) and (x - o_j, x), weights of this group and of the partners
-    for (int j = 0; j < P.ns; j++) {
-      const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
-      const F4 of = mul4(f4s(w.lrc), ldg4(P.ws + j * PL + o));
-      float bv[4];
+    // consistency pairs (x, x + o_j) and (x - o_j, x): weights from the coefficient planes
 #pragma unroll
-      for (int i = 0; i < 4; i++)
-        bv[i] = inside(P, y - dy, x + i - dx) ? w.lrc * P.ws[j * PL + o + i - (long)dy * P.pitch - dx] : 0.f;
-      const F4 ob = f4v(bv[0], bv[1], bv[2], bv[3]);
+    for (int j = 0; j < GID_MAX_PAIRS; j++) {
+      if (j < P.ns) {
+        const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
+        const F4 of = ldg4(cf + (CL::CW + j) * PL), ob = ldg4(cf + (CL::CW + P.ns + j) * PL);
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        const float* fw = &t.pr[c][ry + dy][cx + dx];
-        const float* bw = &t.pr[c][ry - dy][cx - dx];
-        qr[c] = fma4(of, sub4(pcr[c], f4v(fw[0], fw[1], fw[2], fw[3])), qr[c]);
-        qr[c] = fma4(ob, sub4(pcr[c], f4v(bw[0], bw[1], bw[2], bw[3])), qr[c]);
+        for (int c = 0; c < 3; c++) {
+          const float* fw = &t.pr[c][ry + dy][cx + dx];
+          const float* bw = &t.pr[c][ry - dy][cx - dx];
+          qr[c] = fma4(of, sub4(pcr[c], f4v(fw[0], fw[1], fw[2], fw[3])), qr[c]);
+          qr[c] = fma4(ob, sub4(pcr[c], f4v(bw[0], bw[1], bw[2], bw[3])), qr[c]);
+        }
       }
     }
 #pragma unroll
@@ -804,14 +831,17 @@ __global__ void __launch_bounds__(256) k_update(Params P, const float* __restric
     } else if (last == 2) {
       d4[o] = axpy(alpha, p4[o], d4[o]);
     } else {
-      const float4 pv = p4[o], dv = d4[o];
+      // delta, r and M^-1 are touched only here: stream them past L2 (evict first) so
+      // that z, p, q and the coefficient planes the operator step re-reads stay resident.
+      const float4 pv = p4[o];
+      const float4 dv = __ldcs(d4 + o);
       const float4 qv = reinterpret_cast<const float4*>(P.q)[o];
-      const float4 rv = reinterpret_cast<const float4*>(P.r)[o];
-      const float4 mv = reinterpret_cast<const float4*>(P.Minv)[o];
-      d4[o] = axpy(alpha, pv, dv);
+      const float4 rv = __ldcs(reinterpret_cast<const float4*>(P.r) + o);
+      const float4 mv = __ldcs(reinterpret_cast<const float4*>(P.Minv) + o);
+      __stcs(d4 + o, axpy(alpha, pv, dv));
       const float4 rn = axpy(-alpha, qv, rv);
       const float4 zz = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
-      reinterpret_cast<float4*>(P.r)[o] = rn;
+      __stcs(reinterpret_cast<float4*>(P.r) + o, rn);
       reinterpret_cast<float4*>(P.z)[o] = zz;
       rz = rn.x * zz.x + rn.y * zz.y + rn.z * zz.z + rn.w * zz.w;
     }

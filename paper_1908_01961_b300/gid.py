@@ -29,7 +29,7 @@ EXPORTS = (
     "gid_get_base_colors", "gid_set_frame", "gid_init", "gid_run", "gid_get_layers", "gid_get_state",
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
-    "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc",
+    "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
 )
 
 
@@ -90,6 +90,8 @@ def load():
     L.gid_launch_count.argtypes = [P, LL]
     L.gid_profile.argtypes = [P, I]
     L.gid_profile_read.argtypes = [P, D, LL]
+    L.gid_set_apply_tile.argtypes = [P, I]
+    L.gid_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), F]
     L.gid_dense_refine_noalloc.argtypes = [I, I, I, P, P, F, ctypes.POINTER(Weights), P, P, P, P,
                                            ctypes.c_char_p, I]
     for n in EXPORTS:
@@ -267,6 +269,17 @@ class Solver:
         D = ctypes.POINTER(ctypes.c_double)
         self._chk(self.lib.gid_stage_dense_normal(self.h, A.ctypes.data_as(D), g.ctypes.data_as(D)))
         return A, g
+
+    # -- operator tile shape
+    def set_apply_tile(self, rows: int):
+        self._chk(self.lib.gid_set_apply_tile(self.h, rows))
+
+    def autotune(self, reps: int = 10):
+        """Pick the fastest operator tile shape on the current frame; returns (rows, {rows: us})."""
+        rows = ctypes.c_int()
+        us = (ctypes.c_float * 4)()
+        self._chk(self.lib.gid_autotune(self.h, reps, ctypes.byref(rows), us))
+        return rows.value, dict(zip((2, 4, 8, 17), us[:]))
 
     # -- instrumentation
     def launch_count(self) -> int:
