@@ -162,12 +162,15 @@ def ncu_traffic(kernel):
 def algorithmic_bytes(kind, K, P, M, ns, nt, temporal):
     """Minimum bytes each kernel kind moves per launch as designed (FP32 planes)."""
     V = K + 4
-    NC = 10 + 3 * (K + 1)          # operator coefficient planes written by k_linearize
+    NC = 10 + 3 * (K + 1) + 2 * ns  # operator coefficient planes written by k_linearize (pair weights included)
     t = 1 if temporal else 0
-    if kind == "apply":     # read z, coefficients, pair weights (+ p_old, q_old after step 1); write p, q
-        first = 3 * V + NC + ns
-        rest = 5 * V + NC + ns
+    if kind == "apply":     # read z, coefficients (+ p_old, q_old after step 1); write p, q
+        first = 3 * V + NC
+        rest = 5 * V + NC
         return 4.0 * P * ((M - 1) * rest + first) / M
+    if kind == "pcg":       # the persistent loop: M operator phases and M vector phases
+        return M * (algorithmic_bytes("apply", K, P, M, ns, nt, temporal) +
+                    algorithmic_bytes("update", K, P, M, ns, nt, temporal))
     if kind == "update":    # read delta, p, q, r, M^-1; write delta, r, z (last: read delta, p, X; write X)
         return 4.0 * P * ((M - 1) * 8 * V + 4 * V) / M
     if kind == "linearize":  # read X, I, w_SR, pairs (+ r_prev, temporal sum); write M^-1, r, z, delta, coefficients
@@ -286,7 +289,8 @@ def run_gid(args, ws, rank, local):
     dom_ms = kinds[dom][0] / kinds[dom][1]
     alg = algorithmic_bytes(dom, K, P, M, len(off_s), len(off_t), True)
     peak, peak_src = measured_peaks()
-    kernel_name = {"apply": "k_apply", "update": "k_update", "linearize": "k_linearize", "dense": "k_dense"}.get(dom)
+    kernel_name = {"apply": "k_apply", "update": "k_update", "linearize": "k_linearize", "dense": "k_dense",
+                   "pcg": "k_pcg"}.get(dom)
     traffic = ncu_traffic(kernel_name) if kernel_name else None
     roof = None
     if alg:

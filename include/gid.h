@@ -117,8 +117,15 @@ int gid_init(gid_ctx* ctx, int mode);
 
 /* Run n_outer flip-flop iterations (Sec. 6.1): each a Gauss-Newton step of
  * exactly m_inner PCG steps on the layers, then (per refine_base_colors) the
- * base-colour step.  Asynchronous.  n_outer >= 0, m_inner >= 1. */
+ * base-colour step.  Asynchronous.  n_outer >= 0, m_inner >= 1.  The launch
+ * sequence is recorded once per (n_outer, m_inner, refinement, temporal pairs,
+ * tile shape) as a CUDA graph and replayed on a context-owned stream, ordered
+ * after earlier work on the context stream and before later work on it. */
 int gid_run(gid_ctx* ctx, int n_outer, int m_inner);
+
+/* enable = 0: launch gid_run's kernels one by one on the context stream
+ * (profiling does this automatically); 1 (default): graph replay. */
+int gid_set_graphs(gid_ctx* ctx, int enable);
 
 /* Layers of the current state: R_dev (3 x H x W) = exp(r), T_dev ((K+1) x H x W)
  * = T_0..T_K.  Either pointer may be NULL.  Asynchronous. */
@@ -170,17 +177,23 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 
 /* ---- operator tile shape ---- */
 
-/* Rows per tile of the PCG operator kernel: 2, 4 (default), 8 or 17 (128 pixels
- * wide each; 17 runs one 544-thread block per SM).  Results do not depend on
- * it; only speed does. */
+/* How the PCG loop runs.  rows = 2, 4 (default), 8 or 17: one operator kernel
+ * and one vector kernel per PCG step, operator tiles of 128 x rows pixels
+ * (17 runs one 544-thread block per SM).  rows = 0: all PCG steps of a
+ * Gauss-Newton step in one cooperative launch (one block per SM, operator and
+ * vector phases separated by grid barriers whose waits are bounded; a barrier
+ * that gives up is reported as GID_ERR_TIMEOUT by the next synchronising
+ * call); GID_ERR_INVALID_ARG if the device cannot co-schedule it.  Results
+ * agree to FP32 rounding order; only speed differs. */
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
-/* Time reps PCG steps (operator + vector step) with each operator tile shape
- * on the current frame and state (CUDA events on the context stream) and keep
- * the fastest.  Writes the chosen rows to *rows_out and the four timings (us
- * per PCG step, shapes 2, 4, 8, 17) to us_out[4]; either may be NULL.  Needs
- * gid_set_frame and a state; leaves the state X unchanged (the PCG vectors are
- * scratch until the next gid_run).  Call it between runs.  Synchronises. */
+/* Time reps PCG steps with each of the five ways above on the current frame
+ * and state (CUDA events on the context stream) and keep the fastest.  Writes
+ * the chosen rows (0 = persistent) to *rows_out and the five timings (us per
+ * PCG step; shapes 2, 4, 8, 17, persistent, -1 if unavailable) to us_out[5];
+ * either may be NULL.  Needs gid_set_frame and a state; leaves the state X
+ * unchanged (the PCG vectors are scratch until the next gid_run).  Call it
+ * between runs.  Synchronises. */
 int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
 
 /* ---- instrumentation ---- */
@@ -194,7 +207,8 @@ int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
 #define GID_KIND_DENSE 5     /* base-colour normal equations + solve */
 #define GID_KIND_ENERGY 6
 #define GID_KIND_READOUT 7
-#define GID_NUM_KINDS 8
+#define GID_KIND_PCG 8       /* persistent PCG loop (all steps of a Gauss-Newton step) */
+#define GID_NUM_KINDS 9
 
 /* Number of kernels this context has launched since gid_create. */
 int gid_launch_count(const gid_ctx* ctx, long long* n);

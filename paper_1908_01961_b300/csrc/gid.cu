@@ -30,6 +30,8 @@ struct gid_ctx {
   DevColors* col = nullptr;
   DevScalars* sc = nullptr;
   double* partial = nullptr;
+  double* pcg_part = nullptr;
+  int nbmax = 0;
   // staging for the host-buffer entry point (allocated on first use)
   float* st_rgb = nullptr;
   uint8_t* st_lab = nullptr;
@@ -38,6 +40,18 @@ struct gid_ctx {
   int frames_solved = 0;
   long long launches = 0;  // kernels launched by this context
   int apply_th = 4;        // rows per operator tile (gid_set_apply_tile / gid_autotune)
+  int pcg_blocks = 0;      // > 0: run the PCG loop as one cooperative launch of this many blocks
+  bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
+  // CUDA graphs of gid_run's launch sequence, replayed on a context-owned stream
+  struct Graph {
+    int n, m, refine, temporal, th;
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  bool use_graph = true;
+  std::vector<Graph> graphs;
+  cudaStream_t gs = nullptr;
+  cudaEvent_t gev_in = nullptr, gev_out = nullptr;
   // optional per-kernel CUDA-event timing (gid_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
@@ -134,14 +148,19 @@ static Params params(const gid_ctx* c) {
   P.col = c->col;
   P.sc = c->sc;
   P.partial = c->partial;
+  P.pcg_part = c->pcg_part;
+  P.nbmax = c->nbmax;
   return P;
 }
 
 static dim3 pix_grid(const gid_ctx* c) { return dim3((c->W + BX - 1) / BX, (c->H + BY - 1) / BY); }
-static int dense_blocks(const gid_ctx* c) {
-  long P = (long)c->H * c->W;
-  long nb = (P + 256 * 8 - 1) / (256 * 8);
-  return (int)std::max(1L, std::min(nb, 296L));
+static int dense_blocks(const gid_ctx* c) { return std::max(1, std::min(c->H, 296)); }
+// Blocks of the PCG operator step for the context's tile shape.
+static int apply_blocks(const gid_ctx* c) { return ((c->W + VTW - 1) / VTW) * ((c->H + c->apply_th - 1) / c->apply_th); }
+// Blocks of the PCG vector step: a few per SM, striding over the planes.
+static int update_blocks(const gid_ctx* c) {
+  const long items = (long)c->V * (c->plane / 4);
+  return (int)std::max(1L, std::min((items + 255) / 256, 148L * 4));
 }
 
 // ---------------------------------------------------------------- K dispatch
@@ -152,27 +171,57 @@ struct Launch {
     k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg);
   }
   template <int TH>
-  static void apply_th(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
-    static bool attr = false;  // opt in to > 48 KB of dynamic shared memory once per instantiation
+  static void apply_th(const gid_ctx* c, int mode, int first, int it, const float* pin, float* pout, float* qout) {
     const size_t smem = sizeof(ApplyTile<K, TH>);
-    if (!attr) {
-      cudaFuncSetAttribute(k_apply<K, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-      attr = true;
-    }
     const dim3 grid((c->W + VTW - 1) / VTW, (c->H + TH - 1) / TH);
-    k_apply<K, TH><<<grid, dim3(BX, TH), smem, c->stream>>>(params(c), mode, first, pin, pout, qout);
+    k_apply<K, TH><<<grid, dim3(BX, TH), smem, c->stream>>>(params(c), mode, first, it, update_blocks(c), pin, pout,
+                                                             qout);
   }
-  static void apply(const gid_ctx* c, int mode, int first, const float* pin, float* pout, float* qout) {
+  // Opt every operator tile shape in to its dynamic shared memory (before any graph capture).
+  static void prepare(const gid_ctx*) {
+    cudaFuncSetAttribute(k_apply<K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 2>));
+    cudaFuncSetAttribute(k_apply<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 4>));
+    cudaFuncSetAttribute(k_apply<K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 8>));
+    cudaFuncSetAttribute(k_apply<K, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 17>));
+  }
+  static void apply(const gid_ctx* c, int mode, int first, int it, const float* pin, float* pout, float* qout) {
     switch (c->apply_th) {
-      case 2: apply_th<2>(c, mode, first, pin, pout, qout); break;
-      case 4: apply_th<4>(c, mode, first, pin, pout, qout); break;
-      case 17: apply_th<17>(c, mode, first, pin, pout, qout); break;
-      default: apply_th<8>(c, mode, first, pin, pout, qout); break;
+      case 2: apply_th<2>(c, mode, first, it, pin, pout, qout); break;
+      case 4: apply_th<4>(c, mode, first, it, pin, pout, qout); break;
+      case 17: apply_th<17>(c, mode, first, it, pin, pout, qout); break;
+      default: apply_th<8>(c, mode, first, it, pin, pout, qout); break;
     }
   }
-  static void update(const gid_ctx* c, const float* p, int last) {
-    const long n4 = c->plane / 4;
-    k_update<K><<<dim3((unsigned)((n4 + 255) / 256), K + 4), 256, 0, c->stream>>>(params(c), p, last);
+  // The persistent PCG loop: one block per SM of 17 x 32 threads; returns the launch error.
+  static cudaError_t pcg(const gid_ctx* c, int m_inner, int last_mode) {
+    constexpr int TH = 17;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->pcg_blocks);
+    cfg.blockDim = dim3(BX, TH);
+    cfg.dynamicSmemBytes = sizeof(ApplyTile<K, TH>);
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pcg<K, TH>, params(c), m_inner, last_mode, c->pA, c->q);
+  }
+  // Co-resident blocks of the persistent PCG kernel (0 if it cannot run here).
+  static int pcg_capacity(const gid_ctx*) {
+    constexpr int TH = 17;
+    cudaFuncSetAttribute(k_pcg<K, TH>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, TH>));
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg<K, TH>, BX * TH, sizeof(ApplyTile<K, TH>)) !=
+        cudaSuccess)
+      return 0;
+    return coop ? sms * per_sm : 0;
+  }
+  static void update(const gid_ctx* c, int it, const float* p, int last) {
+    k_update<K><<<update_blocks(c), 256, 0, c->stream>>>(params(c), it, apply_blocks(c), p, last);
   }
   static void dense(const gid_ctx* c, int solve) {
     k_dense<K><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
@@ -216,6 +265,7 @@ static int sync_status(gid_ctx* c) {
     GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
     if (st & ST_BAD_LABEL) return fail(c, GID_ERR_INVALID_ARG, "a label was >= K (treated as 0)");
     if (st & ST_SINGULAR) return fail(c, GID_ERR_NUMERIC, "base-colour normal equations not positive definite");
+    if (st & ST_TIMEOUT) return fail(c, GID_ERR_TIMEOUT, "a grid barrier of the persistent PCG kernel gave up waiting");
   }
   return GID_OK;
 }
@@ -290,7 +340,9 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
   const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
   const size_t pbytes = (size_t)npart * sizeof(double);
-  c->pool_bytes = fbytes + lbytes + 256 * 8 + sizeof(DevColors) + sizeof(DevScalars) + pbytes;
+  c->nbmax = (int)std::max({(long)update_blocks(c), (long)((W + VTW - 1) / VTW) * ((H + 1) / 2), 148L * 32});
+  const size_t ppbytes = sizeof(double) * 4 * (size_t)c->nbmax;
+  c->pool_bytes = fbytes + lbytes + 256 * 9 + sizeof(DevColors) + sizeof(DevScalars) + pbytes + ppbytes;
   e = cudaMalloc(&c->pool, c->pool_bytes);
   if (e != cudaSuccess) {
     delete c;
@@ -324,12 +376,27 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->col = (DevColors*)take(sizeof(DevColors));
   c->sc = (DevScalars*)take(sizeof(DevScalars));
   c->partial = (double*)take(pbytes);
+  c->pcg_part = (double*)take(ppbytes);
   if ((size_t)(p - c->pool) > c->pool_bytes) {
     cudaFree(c->pool);
     delete c;
     return fail(nullptr, GID_ERR_OOM, "internal pool layout");
   }
-  e = cudaMemsetAsync(c->pool, 0, c->pool_bytes, c->stream);
+  GID_DISPATCH(c, prepare, c);
+  switch (c->K) {
+    case 1: c->pcg_blocks = Launch<1>::pcg_capacity(c); break;
+    case 2: c->pcg_blocks = Launch<2>::pcg_capacity(c); break;
+    case 3: c->pcg_blocks = Launch<3>::pcg_capacity(c); break;
+    case 4: c->pcg_blocks = Launch<4>::pcg_capacity(c); break;
+    case 5: c->pcg_blocks = Launch<5>::pcg_capacity(c); break;
+    case 6: c->pcg_blocks = Launch<6>::pcg_capacity(c); break;
+    case 7: c->pcg_blocks = Launch<7>::pcg_capacity(c); break;
+    case 8: c->pcg_blocks = Launch<8>::pcg_capacity(c); break;
+    case 9: c->pcg_blocks = Launch<9>::pcg_capacity(c); break;
+    default: c->pcg_blocks = Launch<10>::pcg_capacity(c); break;
+  }
+  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->pool, 0, c->pool_bytes, c->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     cudaFree(c->pool);
@@ -347,6 +414,13 @@ extern "C" void gid_destroy(gid_ctx* c) {
   else
     cudaDeviceSynchronize();
   for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  if (c->gs) {
+    cudaStreamSynchronize(c->gs);
+    cudaStreamDestroy(c->gs);
+    cudaEventDestroy(c->gev_in);
+    cudaEventDestroy(c->gev_out);
+  }
   cudaFree(c->pool);
   cudaFree(c->st_rgb);
   cudaFree(c->st_lab);
@@ -435,19 +509,35 @@ extern "C" int gid_init(gid_ctx* c, int mode) {
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
   if (int rc = check_launch(c, "k_linearize")) return rc;
-  // p and q are updated in place (see k_apply)
+  if (c->persistent && c->pcg_blocks > 0) {
+    cudaError_t e = cudaSuccess;
+    launch(c, GID_KIND_PCG, [&] {
+      switch (c->K) {
+        case 1: e = Launch<1>::pcg(c, m_inner, last_mode); break;
+        case 2: e = Launch<2>::pcg(c, m_inner, last_mode); break;
+        case 3: e = Launch<3>::pcg(c, m_inner, last_mode); break;
+        case 4: e = Launch<4>::pcg(c, m_inner, last_mode); break;
+        case 5: e = Launch<5>::pcg(c, m_inner, last_mode); break;
+        case 6: e = Launch<6>::pcg(c, m_inner, last_mode); break;
+        case 7: e = Launch<7>::pcg(c, m_inner, last_mode); break;
+        case 8: e = Launch<8>::pcg(c, m_inner, last_mode); break;
+        case 9: e = Launch<9>::pcg(c, m_inner, last_mode); break;
+        default: e = Launch<10>::pcg(c, m_inner, last_mode); break;
+      }
+    });
+    if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, "k_pcg (cooperative launch)", cudaGetErrorString(e));
+    return check_launch(c, "k_pcg");
+  }
+  // p and q are updated in place (see k_apply); step m's scalars use partial slots m % 2
   for (int m = 1; m <= m_inner; m++) {
-    launch(c, GID_KIND_APPLY, [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, (const float*)c->pA, c->pA, c->q); });
-    launch(c, GID_KIND_UPDATE, [&] { GID_DISPATCH(c, update, c, (const float*)c->pA, m == m_inner ? last_mode : 0); });
+    launch(c, GID_KIND_APPLY,
+           [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, m, (const float*)c->pA, c->pA, c->q); });
+    launch(c, GID_KIND_UPDATE, [&] { GID_DISPATCH(c, update, c, m, (const float*)c->pA, m == m_inner ? last_mode : 0); });
   }
   return check_launch(c, "pcg");
 }
 
-extern "C" int gid_run(gid_ctx* c, int n_outer, int m_inner) {
-  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
-  if (n_outer < 0 || m_inner < 1) return fail(c, GID_ERR_INVALID_ARG, "n_outer >= 0 and m_inner >= 1");
-  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "gid_run before gid_set_frame / gid_init");
-  const bool refine = c->w.refine_base_colors == 1 || (c->w.refine_base_colors == 2 && c->frames_solved == 0);
+static int enqueue_run(gid_ctx* c, int n_outer, int m_inner, bool refine) {
   for (int n = 0; n < n_outer; n++) {
     if (int rc = enqueue_gn_step(c, m_inner, 1)) return rc;
     if (refine) {
@@ -455,7 +545,71 @@ extern "C" int gid_run(gid_ctx* c, int n_outer, int m_inner) {
       if (int rc = check_launch(c, "k_dense")) return rc;
     }
   }
+  return GID_OK;
+}
+
+// Capture the run's launch sequence once per (N, M, refinement, temporal pairs,
+// tile shape) into a CUDA graph on the context's own stream; replay it fenced
+// by events against the caller's stream (which may be the legacy default
+// stream, where capture is not allowed).
+static int run_graph(gid_ctx* c, int n_outer, int m_inner, bool refine) {
+  if (!c->gs) {
+    GID_TRY_CUDA(c, cudaStreamCreateWithFlags(&c->gs, cudaStreamNonBlocking));
+    GID_TRY_CUDA(c, cudaEventCreateWithFlags(&c->gev_in, cudaEventDisableTiming));
+    GID_TRY_CUDA(c, cudaEventCreateWithFlags(&c->gev_out, cudaEventDisableTiming));
+  }
+  const int temporal = c->temporal_active ? 1 : 0;
+  gid_ctx::Graph* g = nullptr;
+  for (auto& e : c->graphs)
+    if (e.n == n_outer && e.m == m_inner && e.refine == (int)refine && e.temporal == temporal && e.th == c->apply_th)
+      g = &e;
+  if (!g) {
+    cudaStream_t user = c->stream;
+    const long long l0 = c->launches;
+    GID_TRY_CUDA(c, cudaStreamBeginCapture(c->gs, cudaStreamCaptureModeThreadLocal));
+    c->stream = c->gs;
+    int rc = enqueue_run(c, n_outer, m_inner, refine);
+    c->stream = user;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(c->gs, &graph);
+    if (rc) {
+      if (graph) cudaGraphDestroy(graph);
+      c->launches = l0;
+      return rc;
+    }
+    if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, "cudaStreamEndCapture", cudaGetErrorString(e));
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, "cudaGraphInstantiate", cudaGetErrorString(e));
+    c->graphs.push_back({n_outer, m_inner, (int)refine, temporal, c->apply_th, exec, c->launches - l0});
+    c->launches = l0;
+    g = &c->graphs.back();
+  }
+  GID_TRY_CUDA(c, cudaEventRecord(c->gev_in, c->stream));
+  GID_TRY_CUDA(c, cudaStreamWaitEvent(c->gs, c->gev_in, 0));
+  GID_TRY_CUDA(c, cudaGraphLaunch(g->exec, c->gs));
+  GID_TRY_CUDA(c, cudaEventRecord(c->gev_out, c->gs));
+  GID_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, c->gev_out, 0));
+  c->launches += g->kernels;
+  return GID_OK;
+}
+
+extern "C" int gid_run(gid_ctx* c, int n_outer, int m_inner) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (n_outer < 0 || m_inner < 1) return fail(c, GID_ERR_INVALID_ARG, "n_outer >= 0 and m_inner >= 1");
+  if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "gid_run before gid_set_frame / gid_init");
+  const bool refine = c->w.refine_base_colors == 1 || (c->w.refine_base_colors == 2 && c->frames_solved == 0);
+  int rc = (c->use_graph && !c->prof && n_outer > 0) ? run_graph(c, n_outer, m_inner, refine)
+                                                      : enqueue_run(c, n_outer, m_inner, refine);
+  if (rc) return rc;
   c->frames_solved++;
+  return GID_OK;
+}
+
+extern "C" int gid_set_graphs(gid_ctx* c, int enable) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  c->use_graph = enable != 0;
   return GID_OK;
 }
 
@@ -574,7 +728,7 @@ extern "C" int gid_stage_apply(gid_ctx* c, const float* p_dev, float* q_dev) {
   if (int rc = to_pitched(c, c->pA, p_dev)) return rc;
   launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 2, (float*)nullptr, (float*)nullptr); });
   launch(c, GID_KIND_APPLY,
-         [&] { GID_DISPATCH(c, apply, c, 1, 0, (const float*)c->pA, (float*)nullptr, c->pB); });
+         [&] { GID_DISPATCH(c, apply, c, 1, 0, 1, (const float*)c->pA, (float*)nullptr, c->pB); });
   if (int rc = check_launch(c, "k_apply")) return rc;
   return from_pitched(c, q_dev, c->pB);
 }
@@ -638,9 +792,15 @@ extern "C" int gid_profile_read(gid_ctx* c, double* ms, long long* count) {
 
 extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (rows == 0) {
+    if (c->pcg_blocks <= 0) return fail(c, GID_ERR_INVALID_ARG, "the persistent PCG kernel cannot run on this device");
+    c->persistent = true;
+    return GID_OK;
+  }
   if (rows != 2 && rows != 4 && rows != 8 && rows != 17)
-    return fail(c, GID_ERR_INVALID_ARG, "tile rows must be 2, 4, 8 or 17");
+    return fail(c, GID_ERR_INVALID_ARG, "tile rows must be 0 (persistent), 2, 4, 8 or 17");
   c->apply_th = rows;
+  c->persistent = false;
   return GID_OK;
 }
 
@@ -659,12 +819,16 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
   const int cand[4] = {2, 4, 8, 17};
   float best = 1e30f;
   int best_th = c->apply_th;
+  c->persistent = false;
   for (int i = 0; i < 4; i++) {
     c->apply_th = cand[i];
+    int it = 0;
     auto pair = [&](int first) {
-      GID_DISPATCH(c, apply, c, 0, first, (const float*)c->pA, c->pA, c->q);
-      GID_DISPATCH(c, update, c, (const float*)c->pA, 0);
+      ++it;
+      GID_DISPATCH(c, apply, c, 0, first, it, (const float*)c->pA, c->pA, c->q);
+      GID_DISPATCH(c, update, c, it, (const float*)c->pA, 0);
     };
+    GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr);
     pair(1);
     pair(0);
     cudaEventRecord(e0, c->stream);
@@ -682,9 +846,28 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
       best_th = cand[i];
     }
   }
+  c->apply_th = best_th;
+  // the persistent PCG kernel (tile rows 17, one block per SM): reps + 2 steps in one launch
+  bool pers = false;
+  if (c->pcg_blocks > 0) {
+    c->persistent = true;
+    if (int rc = enqueue_gn_step(c, 2, 2)) return rc;
+    cudaEventRecord(e0, c->stream);
+    if (int rc = enqueue_gn_step(c, reps + 2, 2)) return rc;
+    cudaEventRecord(e1, c->stream);
+    GID_TRY_CUDA(c, cudaEventSynchronize(e1));
+    float ms = 0.f;
+    GID_TRY_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+    const float us = 1000.f * ms / (reps + 2);
+    if (us_out) us_out[4] = us;
+    pers = us < best;
+    c->persistent = pers;
+    if (int rc = sync_status(c)) return rc;
+  } else if (us_out) {
+    us_out[4] = -1.f;
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  c->apply_th = best_th;
-  if (rows_out) *rows_out = best_th;
+  if (rows_out) *rows_out = pers ? 0 : best_th;
   return GID_OK;
 }

@@ -37,17 +37,18 @@ struct DevColors {
   double bd[GID_MAX_K * 3];
 };
 
-enum : int { ST_BAD_LABEL = 1, ST_SINGULAR = 2 };
+enum : int { ST_BAD_LABEL = 1, ST_SINGULAR = 2, ST_TIMEOUT = 4 };
 
 struct DevScalars {
   double rho, pq, alpha, beta;
+  double rho2[2];  // rho of PCG step m in slot m % 2 (see k_apply)
   double energy[8];
   double A[3 * GID_MAX_K * GID_MAX_K];
   double g[3 * GID_MAX_K];
   unsigned int cnt[8];
   int status;
 };
-enum { CNT_LIN, CNT_APPLY, CNT_UPDATE, CNT_DENSE, CNT_ENERGY };
+enum { CNT_LIN, CNT_APPLY, CNT_UPDATE, CNT_DENSE, CNT_ENERGY, CNT_GRID, CNT_GEN };
 
 struct Params {
   int H, W, pitch;
@@ -73,6 +74,8 @@ struct Params {
   DevColors* col;
   DevScalars* sc;
   double* partial;
+  double* pcg_part;  // [2 kinds: operator <p,q>, vector <r,z>][2 parities][nbmax] block partials
+  int nbmax;
 };
 
 // ---------------------------------------------------------------- reductions
@@ -151,6 +154,41 @@ __device__ __forceinline__ double grid_total(const double* partial, int n, int s
   for (; i < n; i += nt) s += __ldcg(partial + (long)i * stride + base);
   return block_sum(s);
 }
+
+// The PCG scalars are formed by the kernel that consumes them: every block sums
+// the previous kernel's block partials in the same fixed order (so all blocks
+// agree bit for bit), and no kernel of the PCG loop has a serial last-block
+// tail.  part_share is a thread's share (loads issued early), block_total the
+// block-wide sum returned to every thread.
+__device__ __forceinline__ double part_share(const double* part, int n) {
+  double s = 0.0;
+  const int nt = blockDim.x * blockDim.y;
+  for (int i = tid_flat(); i < n; i += nt) s += __ldcg(part + i);
+  return s;
+}
+
+__device__ __forceinline__ double block_total(double v) {
+  __shared__ double sh[32];
+  __shared__ double tot;
+  const int t = tid_flat(), lane = t & 31, wid = t >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  if (lane == 0) sh[wid] = v;
+  __syncthreads();
+  if (t == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nw; i++) s += sh[i];
+    tot = s;
+  }
+  __syncthreads();
+  return tot;
+}
+
+__device__ __forceinline__ double* pcg_partials(const Params& P, int kind, int it) {
+  return P.pcg_part + ((long)kind * 2 + (it & 1)) * P.nbmax;
+}
+enum { PART_PQ = 0, PART_RZ = 1 };
 
 // ---------------------------------------------------------------- IRLS weights (Sec. 5.3)
 
@@ -557,7 +595,9 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
     const double t = grid_total(P.partial, nb, 1, 0);
     if (tid_flat() == 0) {
       P.sc->rho = t;
+      P.sc->rho2[1] = t;  // rho of PCG step 1
       P.sc->beta = 0.0;
+      P.sc->cnt[CNT_GRID] = 0u;  // arrival counter of the persistent PCG kernel's grid barrier
     }
   }
 }
@@ -625,25 +665,25 @@ struct ApplyShape<17> {
   static constexpr int MINB = 1, MAXREG = 96;
 };
 
-// PCG operator step: p = z + beta p_old (first step: p = z), q = J^T J p from
-// the step's coefficient planes, <p, q> reduced, alpha = rho / <p, q>.  The
+// PCG operator step it: p = z + beta p_old (first step: p = z), q = J^T J p
+// from the step's coefficient planes, block partials of <p, q>.  The
 // stencil is applied to z only: q = J^T J z + beta q_old equals J^T J p since
 // J^T J is fixed within a Gauss-Newton step, so only z needs a halo and p_old,
 // q_old are read at the thread's own pixels (p and q may be updated in place).
 // mode 1 (stage): q = J^T J pin.  Padding columns (W <= x < pitch) of p, q, z
 // and of every coefficient plane are zero and stay zero.
-template <int K, int TH>
-__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
-    k_apply(Params P, int mode, int first, const float* pin, float* pout, float* __restrict__ qout) {
+// One operator tile (origin x0, y0): stage s, then q = A s (+ beta q_old) and
+// p = s (+ beta p_old) on the tile's pixels.  get_beta() is called once the
+// staging loads are in (it may wait on a block reduction).  Returns this
+// thread's share of <p, q>.  All threads of the block call it.
+template <int K, int TH, class GB>
+__device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t, const ColorTable<K>& ct, int x0, int y0,
+                                            int mode, int first, GB get_beta, const float* pin, float* pout,
+                                            float* __restrict__ qout) {
   using CL = CoefLayout<K>;
   constexpr int NCH = VRW / 4;  // float4 chunks per staged row
   constexpr int NTH = BX * TH;  // threads per block
-  extern __shared__ float4 apply_smem[];
-  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
-  __shared__ ColorTable<K> ct;
-  load_colors<K>(ct, P.col);
-  const float beta = (mode == 0 && !first) ? (float)P.sc->beta : 0.f;
-  const int x0 = blockIdx.x * VTW, y0 = blockIdx.y * TH, tid = tid_flat();
+  const int tid = tid_flat();
   // Stage s = z (PCG step) or s = pin (stage call) with its halo.  Each thread
   // issues up to SB chunk loads before storing any, so a block needs only a
   // couple of memory round trips.
@@ -686,6 +726,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     }
   }
   __syncthreads();
+  const float beta = get_beta();
   float pq = 0.f;
   const int y = y0 + threadIdx.y, x = x0 + QW * threadIdx.x;
   if (x < P.W && y < P.H) {
@@ -790,73 +831,203 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
       finish(3 + k, pk, q);
     }
   }
+  return pq;
+}
+
+template <int K, int TH>
+__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
+    k_apply(Params P, int mode, int first, int it, int nb_prev, const float* pin, float* pout,
+            float* __restrict__ qout) {
+  extern __shared__ float4 apply_smem[];
+  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
+  __shared__ ColorTable<K> ct;
+  load_colors<K>(ct, P.col);
+  const bool use_beta = mode == 0 && !first;
+  // this thread's share of rho_it = <r, z> from the previous vector step's partials
+  const double rho_share = use_beta ? part_share(pcg_partials(P, PART_RZ, it - 1), nb_prev) : 0.0;
+  // beta = rho_it / rho_(it-1); block (0, 0) records rho_it for the vector step
+  auto get_beta = [&]() -> float {
+    if (!use_beta) return 0.f;
+    const double rho = block_total(rho_share), rho_old = P.sc->rho2[(it - 1) & 1];
+    if (tid_flat() == 0 && blockIdx.x == 0 && blockIdx.y == 0) P.sc->rho2[it & 1] = rho;
+    return rho_old != 0.0 ? (float)(rho / rho_old) : 0.f;
+  };
+  const float pq = apply_tile<K, TH>(P, t, ct, blockIdx.x * VTW, blockIdx.y * TH, mode, first, get_beta, pin, pout, qout);
   if (mode != 0) return;
   const double bs = block_sum_f(pq);
-  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
-  if (tid == 0) P.partial[b] = bs;
-  if (last_block(&P.sc->cnt[CNT_APPLY])) {
-    const double tt = grid_total(P.partial, nb, 1, 0);
-    if (tid == 0) {
-      P.sc->pq = tt;
-      P.sc->alpha = tt != 0.0 ? P.sc->rho / tt : 0.0;
-    }
-  }
+  if (tid_flat() == 0) pcg_partials(P, PART_PQ, it)[blockIdx.y * gridDim.x + blockIdx.x] = bs;
 }
 
 // ---------------------------------------------------------------- PCG vector step
 
-// delta += alpha p, r -= alpha q, z = M^-1 r, rho' = <r, z>, beta = rho' / rho.
+// PCG vector step it: alpha = rho / <p, q>; delta += alpha p, r -= alpha q,
+// z = M^-1 r, block partials of rho' = <r, z>.
 // last 1: X += delta + alpha p (the Gauss-Newton update); last 2: write delta
 // only.  Works on whole pitched planes as float4 (the padding columns of every
-// PCG vector are zero and stay zero).  Grid (plane / 4 / 256, V): one float4
-// of one plane per thread, for enough independent loads in flight.
+// PCG vector are zero and stay zero).  A grid of a few blocks per SM strides
+// over all V x plane / 4 float4 items, UF items per thread in flight, so that
+// only a few hundred blocks pay for the block reduction and the grid fence.
 template <int K>
-__global__ void __launch_bounds__(256) k_update(Params P, const float* __restrict__ p, int last) {
-  const float alpha = (float)P.sc->alpha;
-  const long n4 = P.plane >> 2;
-  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long o = (long)blockIdx.y * n4 + i;
+__device__ __forceinline__ float update_range(const Params& P, const float* __restrict__ p, float alpha, int last,
+                                              long start, long stride) {
+  constexpr int V = K + 4, UF = 2;
+  const long n4 = P.plane >> 2, total = (long)V * n4;
   const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
   float4* __restrict__ d4 = reinterpret_cast<float4*>(P.d);
+  float4* __restrict__ r4 = reinterpret_cast<float4*>(P.r);
+  float4* __restrict__ z4 = reinterpret_cast<float4*>(P.z);
+  float4* __restrict__ X4 = reinterpret_cast<float4*>(P.X);
+  const float4* __restrict__ q4 = reinterpret_cast<const float4*>(P.q);
+  const float4* __restrict__ m4 = reinterpret_cast<const float4*>(P.Minv);
   float rz = 0.f;
   auto axpy = [](float a, float4 x, float4 y) {
     return make_float4(fmaf(a, x.x, y.x), fmaf(a, x.y, y.y), fmaf(a, x.z, y.z), fmaf(a, x.w, y.w));
   };
-  if (i < n4) {
+  for (long base = start; base < total; base += UF * stride) {
     if (last == 1) {
-      float4* __restrict__ X4 = reinterpret_cast<float4*>(P.X);
-      const float4 dn = axpy(alpha, p4[o], d4[o]);
-      const float4 xv = X4[o];
-      X4[o] = make_float4(xv.x + dn.x, xv.y + dn.y, xv.z + dn.z, xv.w + dn.w);
+#pragma unroll
+      for (int u = 0; u < UF; u++) {
+        const long o = base + u * stride;
+        if (o < total) {
+          const float4 dn = axpy(alpha, p4[o], d4[o]);
+          const float4 xv = X4[o];
+          X4[o] = make_float4(xv.x + dn.x, xv.y + dn.y, xv.z + dn.z, xv.w + dn.w);
+        }
+      }
     } else if (last == 2) {
-      d4[o] = axpy(alpha, p4[o], d4[o]);
+#pragma unroll
+      for (int u = 0; u < UF; u++) {
+        const long o = base + u * stride;
+        if (o < total) d4[o] = axpy(alpha, p4[o], d4[o]);
+      }
     } else {
       // delta, r and M^-1 are touched only here: stream them past L2 (evict first) so
       // that z, p, q and the coefficient planes the operator step re-reads stay resident.
-      const float4 pv = p4[o];
-      const float4 dv = __ldcs(d4 + o);
-      const float4 qv = reinterpret_cast<const float4*>(P.q)[o];
-      const float4 rv = __ldcs(reinterpret_cast<const float4*>(P.r) + o);
-      const float4 mv = __ldcs(reinterpret_cast<const float4*>(P.Minv) + o);
-      __stcs(d4 + o, axpy(alpha, pv, dv));
-      const float4 rn = axpy(-alpha, qv, rv);
-      const float4 zz = make_float4(mv.x * rn.x, mv.y * rn.y, mv.z * rn.z, mv.w * rn.w);
-      __stcs(reinterpret_cast<float4*>(P.r) + o, rn);
-      reinterpret_cast<float4*>(P.z)[o] = zz;
-      rz = rn.x * zz.x + rn.y * zz.y + rn.z * zz.z + rn.w * zz.w;
+      float4 pv[UF], dv[UF], qv[UF], rv[UF], mv[UF];
+#pragma unroll
+      for (int u = 0; u < UF; u++) {
+        const long o = base + u * stride;
+        if (o < total) {
+          pv[u] = p4[o];
+          dv[u] = __ldcs(d4 + o);
+          qv[u] = q4[o];
+          rv[u] = __ldcs(r4 + o);
+          mv[u] = __ldcs(m4 + o);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < UF; u++) {
+        const long o = base + u * stride;
+        if (o < total) {
+          __stcs(d4 + o, axpy(alpha, pv[u], dv[u]));
+          const float4 rn = axpy(-alpha, qv[u], rv[u]);
+          const float4 zz = make_float4(mv[u].x * rn.x, mv[u].y * rn.y, mv[u].z * rn.z, mv[u].w * rn.w);
+          __stcs(r4 + o, rn);
+          z4[o] = zz;
+          rz += rn.x * zz.x + rn.y * zz.y + rn.z * zz.z + rn.w * zz.w;
+        }
+      }
     }
   }
+  return rz;
+}
+
+// PCG vector step it: alpha = rho / <p, q>; delta += alpha p, r -= alpha q,
+// z = M^-1 r, block partials of rho' = <r, z>.  last 1: X += delta + alpha p
+// (the Gauss-Newton update); last 2: write delta only.  Works on whole pitched
+// planes as float4 (the padding columns of every PCG vector are zero and stay
+// zero).  A grid of a few blocks per SM strides over all V x plane / 4 float4
+// items.
+template <int K>
+__global__ void __launch_bounds__(256) k_update(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
+  // alpha = rho_it / <p, q>_it from the operator step's partials
+  const double pq = block_total(part_share(pcg_partials(P, PART_PQ, it), nb_prev));
+  const float alpha = pq != 0.0 ? (float)(P.sc->rho2[it & 1] / pq) : 0.f;
+  const float rz = update_range<K>(P, p, alpha, last, (long)blockIdx.x * blockDim.x + threadIdx.x,
+                                   (long)gridDim.x * blockDim.x);
   if (last) return;
   const double bs = block_sum_f(rz);
-  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
-  if (threadIdx.x == 0) P.partial[b] = bs;
-  if (last_block(&P.sc->cnt[CNT_UPDATE])) {
-    const double tt = grid_total(P.partial, nb, 1, 0);
-    if (threadIdx.x == 0) {
-      const double rho = P.sc->rho;
-      P.sc->beta = rho != 0.0 ? tt / rho : 0.0;
-      P.sc->rho = tt;
+  if (threadIdx.x == 0) pcg_partials(P, PART_RZ, it)[blockIdx.x] = bs;
+}
+
+// ---------------------------------------------------------------- persistent PCG
+
+// Grid-wide barrier of a cooperative launch (all blocks co-resident).  Thread 0
+// of each block arrives on a counter; the last to arrive resets it and bumps a
+// generation word the others wait on.  Every wait is bounded: after GRID_SPINS
+// polls the block records ST_TIMEOUT and the barrier returns false, and the
+// kernel then returns (so it always terminates).
+constexpr long GRID_SPINS = 1L << 22;
+
+__device__ __forceinline__ bool grid_sync(DevScalars* sc) {
+  __shared__ int ok;
+  __syncthreads();
+  if (tid_flat() == 0) {
+    volatile unsigned int* gen = &sc->cnt[CNT_GEN];
+    const unsigned int g = *gen;
+    __threadfence();
+    const unsigned int n = gridDim.x * gridDim.y;
+    if (atomicAdd(&sc->cnt[CNT_GRID], 1u) == n - 1) {
+      sc->cnt[CNT_GRID] = 0u;
+      __threadfence();
+      atomicAdd(&sc->cnt[CNT_GEN], 1u);
+      ok = 1;
+    } else {
+      long spins = 0;
+      while (*gen == g && spins < GRID_SPINS) {
+        __nanosleep(64);
+        spins++;
+      }
+      ok = *gen != g;
+      if (!ok) atomicOr(&sc->status, ST_TIMEOUT);
     }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// All m_inner PCG steps of one Gauss-Newton step in one cooperative launch
+// (one block per SM): operator phase (tiles of ATW x TH pixels, grid-strided),
+// grid barrier, vector phase (grid-strided float4 items), grid barrier.  Every
+// block forms alpha and beta itself from the phase's block partials in the same
+// fixed order, so no block waits on a serial reduction and all agree bit for
+// bit.  p and q are updated in place.  last_mode as for k_update.
+template <int K, int TH>
+__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
+    k_pcg(Params P, int m_inner, int last_mode, float* p, float* __restrict__ q) {
+  extern __shared__ float4 apply_smem[];
+  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
+  __shared__ ColorTable<K> ct;
+  load_colors<K>(ct, P.col);
+  const int nb = gridDim.x, b = blockIdx.x, tid = tid_flat();
+  const int ntx = (P.W + VTW - 1) / VTW, ntiles = ntx * ((P.H + TH - 1) / TH);
+  double* part_pq = pcg_partials(P, PART_PQ, 0);
+  double* part_rz = pcg_partials(P, PART_RZ, 0);
+  double rho = P.sc->rho, rho_old = 0.0;
+  for (int m = 1; m <= m_inner; m++) {
+    const int first = m == 1;
+    const float beta = first ? 0.f : (rho_old != 0.0 ? (float)(rho / rho_old) : 0.f);
+    float pq = 0.f;
+    for (int tile = b; tile < ntiles; tile += nb) {
+      pq += apply_tile<K, TH>(P, t, ct, (tile % ntx) * VTW, (tile / ntx) * TH, 0, first, [&]() { return beta; }, p, p,
+                              q);
+      __syncthreads();  // the next tile re-stages shared memory
+    }
+    double bs = block_sum_f(pq);
+    if (tid == 0) part_pq[b] = bs;
+    if (!grid_sync(P.sc)) return;
+    const double pqs = block_total(part_share(part_pq, nb));
+    const float alpha = pqs != 0.0 ? (float)(rho / pqs) : 0.f;
+    const int last = m == m_inner ? last_mode : 0;
+    const float rz = update_range<K>(P, p, alpha, last, (long)b * blockDim.x * blockDim.y + tid,
+                                     (long)nb * blockDim.x * blockDim.y);
+    if (last) break;
+    bs = block_sum_f(rz);
+    if (tid == 0) part_rz[b] = bs;
+    if (!grid_sync(P.sc)) return;
+    rho_old = rho;
+    rho = block_total(part_share(part_rz, nb));
   }
 }
 
@@ -866,7 +1037,8 @@ __global__ void __launch_bounds__(256) k_update(Params P, const float* __restric
 // normal matrix A_c = l_data sum_x R_c^2 T_k T_l + (l_IR + l_CR) I and
 // g_c = l_data sum_x R_c T_k e_c, e_c the data residual at the initial colours;
 // the last block solves the three SPD systems by FP64 Cholesky and sets
-// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel; 256 threads.
+// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel, blocks
+// stride over rows; 256 threads.
 // Partials: (K (K + 1) / 2 + K) values x (3 nblk) blocks doubles, value-major.
 template <int K>
 __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
@@ -876,13 +1048,11 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
   __shared__ double tot[3][NACC];
   load_colors<K>(ct, P.col);
   const int c = blockIdx.y;
-  const long HW = (long)P.H * P.W;
   float acc[NACC];
 #pragma unroll
   for (int i = 0; i < NACC; i++) acc[i] = 0.f;
-  const long stride = (long)gridDim.x * blockDim.x;
-  for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < HW; i += stride) {
-    const int y = (int)(i / P.W), x = (int)(i - (long)y * P.W);
+  for (int y = blockIdx.x; y < P.H; y += gridDim.x)
+    for (int x = threadIdx.x; x < P.W; x += blockDim.x) {
     const long o = off2(P, y, x);
     const float R = expf(P.X[c * P.plane + o]);
     float T[K + 1];
@@ -902,8 +1072,8 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
       for (int l = 0; l <= k; l++) acc[n++] += a[k] * a[l];
 #pragma unroll
     for (int k = 0; k < K; k++) acc[NA + k] += a[k] * e;
-  }
-  // block reduction: FP64 warp shuffles, then the 8 warp sums in order
+    }
+  // block reduction: FP32 warp shuffles, then the 8 warp sums in order
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
   for (int i = 0; i < NACC; i++) {

@@ -36,7 +36,7 @@ using namespace gid;
 
 namespace {
 
-constexpr int kMaxDenseBlocks = 296;                                   // 2 x 148 SMs
+constexpr int kMaxDenseBlocks = 296;                                   // at most 296 row-striding blocks
 constexpr int kMaxAcc = GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K;   // per-channel accumulators
 constexpr size_t kOffScalars = 0;
 constexpr size_t kOffColors = (sizeof(DevScalars) + 255) / 256 * 256;
@@ -104,7 +104,7 @@ extern "C" int gid_dense_refine_noalloc(int H, int W, int K, const float* X_dev,
   if (H < 1 || W < 1 || (long)H * W > (1L << 28))
     return noalloc_fail(eo, GID_ERR_INVALID_ARG, "H x W must be in 1..2^28 pixels");
   const long P = (long)H * W;
-  const int nblk = (int)std::max(1L, std::min((P + 256 * 8 - 1) / (256 * 8), (long)kMaxDenseBlocks));
+  const int nblk = std::max(1, std::min(H, kMaxDenseBlocks));  // rows per block, as the context path
   const size_t need = kOffPartial + sizeof(double) * (size_t)nblk * 3 * (K * (K + 1) / 2 + K);
   if (need > GID_NOALLOC_SCRATCH_BYTES)
     return noalloc_fail(eo, GID_ERR_INVALID_ARG, "problem needs more scratch than GID_NOALLOC_SCRATCH_BYTES");

@@ -21,7 +21,7 @@ ERRORS = {-1: "GID_ERR_INVALID_ARG", -2: "GID_ERR_CUDA", -3: "GID_ERR_OOM", -4: 
 MAX_K = 10
 MAX_PAIRS = 8
 TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness", "non_neg")
-KINDS = ("frame", "init", "linearize", "apply", "update", "dense", "energy", "readout")
+KINDS = ("frame", "init", "linearize", "apply", "update", "dense", "energy", "readout", "pcg")
 
 # Every function include/gid.h declares.
 EXPORTS = (
@@ -30,6 +30,7 @@ EXPORTS = (
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
+    "gid_set_graphs",
 )
 
 
@@ -91,6 +92,7 @@ def load():
     L.gid_profile.argtypes = [P, I]
     L.gid_profile_read.argtypes = [P, D, LL]
     L.gid_set_apply_tile.argtypes = [P, I]
+    L.gid_set_graphs.argtypes = [P, I]
     L.gid_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), F]
     L.gid_dense_refine_noalloc.argtypes = [I, I, I, P, P, F, ctypes.POINTER(Weights), P, P, P, P,
                                            ctypes.c_char_p, I]
@@ -210,6 +212,9 @@ class Solver:
     def run(self, n_outer: int, m_inner: int):
         self._chk(self.lib.gid_run(self.h, n_outer, m_inner))
 
+    def set_graphs(self, enable: bool):
+        self._chk(self.lib.gid_set_graphs(self.h, 1 if enable else 0))
+
     def layers(self, R=None, T=None):
         R = self._dev((3, self.H, self.W)) if R is None else R
         T = self._dev((self.K + 1, self.H, self.W)) if T is None else T
@@ -275,11 +280,12 @@ class Solver:
         self._chk(self.lib.gid_set_apply_tile(self.h, rows))
 
     def autotune(self, reps: int = 10):
-        """Pick the fastest operator tile shape on the current frame; returns (rows, {rows: us})."""
+        """Pick the fastest PCG execution (tile rows, 0 = persistent) on the current frame;
+        returns (rows, {rows: us per PCG step})."""
         rows = ctypes.c_int()
-        us = (ctypes.c_float * 4)()
+        us = (ctypes.c_float * 5)()
         self._chk(self.lib.gid_autotune(self.h, reps, ctypes.byref(rows), us))
-        return rows.value, dict(zip((2, 4, 8, 17), us[:]))
+        return rows.value, dict(zip((2, 4, 8, 17, 0), us[:]))
 
     # -- instrumentation
     def launch_count(self) -> int:

@@ -203,3 +203,58 @@ def test_errors_are_reported():
     assert e.value.code == -1
     with pytest.raises(gid.GidError):
         s.set_base_colors(np.zeros((case.K, 3)))
+
+
+def test_graph_replay_matches_direct_launches():
+    """gid_run replays a captured CUDA graph; it must give the bits the direct launches give."""
+    case = Case(H=48, W=64, K=4, n_cells=12, seed=6, frames=2, temporal=True)
+    out = []
+    for graphs in (False, True):
+        s = case.solver()
+        s.set_graphs(graphs)
+        for t in range(2):
+            rgb, lab = case.gpu_inputs(t)
+            s.set_frame(rgb, lab)
+            s.init(0 if t == 0 else 1)
+            s.run(3, 7)
+        out.append((s.state().cpu().numpy(), s.base_colors(), s.launch_count()))
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][1], out[1][1])
+    assert out[0][2] == out[1][2]
+
+
+@pytest.mark.parametrize("rows", [2, 4, 8, 17])
+def test_operator_tile_shapes_agree(rows):
+    """Every operator tile shape computes the same J^T J p (up to FP32 rounding order)."""
+    case = Case(**CASES["70x41_K6"], seed=3)
+    s = case.solver()
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    pb = case.oracle_problem()
+    X = random_state(case, pb, 1)
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    s.set_apply_tile(rows)
+    p = np.random.default_rng(2).normal(size=X.shape).astype(np.float32)
+    q = s.stage_apply(torch.from_numpy(p).cuda())
+    close(q.cpu().numpy(), pb.apply(X, f32(p)), what=f"J^T J p, {rows} rows")
+
+
+@pytest.mark.parametrize("name", ["64x48_K4", "70x41_K6"])
+def test_persistent_pcg_matches_oracle(name):
+    """All PCG steps of a Gauss-Newton step in one cooperative launch (grid
+    barriers between the operator and vector phases): same bar as the
+    multi-kernel path."""
+    case = Case(**CASES[name], seed=0)
+    s = case.solver()
+    s.set_apply_tile(0)
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    s.init(0)
+    s.run(5, 10)
+    R, T = s.layers()
+    E, _ = s.energy()
+    pb = case.oracle_problem()
+    Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), 5, 10)
+    assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
+    assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
+    assert np.abs(s.base_colors() - bo).max() <= 1e-3
+    assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
