@@ -196,6 +196,41 @@ int gid_set_apply_tile(gid_ctx* ctx, int rows);
  * between runs.  Synchronises. */
 int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
 
+/* ---- batches of videos (many videos of uneven size, one graph per step) ---- */
+
+typedef struct gid_batch gid_batch;
+
+/* n videos, video i of H[i] x W[i] with K[i] base colours.  w points to one
+ * gid_weights for all (per_video = 0) or to n of them (per_video = 1); NULL for
+ * the defaults.  Each video gets its own context and CUDA stream; stream is
+ * the caller's stream the batch calls are ordered with (NULL: legacy default). */
+int gid_batch_create(int n, const int* H, const int* W, const int* K, const gid_weights* w, int per_video,
+                     void* stream, gid_batch** out);
+void gid_batch_destroy(gid_batch* batch);
+const char* gid_batch_last_error(const gid_batch* batch);
+
+/* Video i's context, for gid_set_base_colors / gid_get_layers / gid_energy...
+ * (those calls then run on the video's own stream).  NULL if i is out of range. */
+gid_ctx* gid_batch_ctx(gid_batch* batch, int i);
+
+/* gid_set_frame / gid_init / gid_new_sequence for every video (arrays of n
+ * device pointers, as gid_set_frame). */
+int gid_batch_set_frames(gid_batch* batch, const float* const* rgb_dev, const uint8_t* const* labels_dev);
+int gid_batch_init(gid_batch* batch, int mode);
+int gid_batch_new_sequence(gid_batch* batch);
+
+/* gid_run(n_outer, m_inner) for every video as ONE CUDA graph launch: each
+ * video's launch sequence is a branch of the graph (recorded once per
+ * configuration), so the videos' kernels run concurrently.  Batches always use
+ * the multi-kernel PCG (tile rows 2, 4, 8 or 17).  Asynchronous. */
+int gid_batch_run(gid_batch* batch, int n_outer, int m_inner);
+
+/* Choose every video's operator tile shape: from the cache file (lines
+ * "H W K rows") if it lists the video's shape, else by gid_autotune(reps) on
+ * the video's current frame and state, then append the new shapes to the file
+ * (cache_path may be NULL: no cache).  Needs frames and states.  Synchronises. */
+int gid_batch_autotune(gid_batch* batch, const char* cache_path, int reps);
+
 /* ---- instrumentation ---- */
 
 /* Kernel kinds for gid_profile_read. */

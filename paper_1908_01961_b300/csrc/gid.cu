@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -869,5 +870,245 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rows_out) *rows_out = pers ? 0 : best_th;
+  return GID_OK;
+}
+
+// ---------------------------------------------------------------- batches of videos
+
+struct gid_batch {
+  int n = 0;
+  std::vector<gid_ctx*> ctx;
+  std::vector<cudaStream_t> streams;  // one per video; the contexts run on these
+  cudaStream_t user = nullptr;        // the caller's stream
+  cudaStream_t bs = nullptr;          // capture / replay stream of the batch graph
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  struct Graph {
+    std::string key;
+    cudaGraphExec_t exec;
+    long long kernels;
+  };
+  std::vector<Graph> graphs;
+  std::string err;
+};
+
+static std::string g_batch_err;
+
+static int bfail(gid_batch* b, int code, const std::string& m) {
+  if (b)
+    b->err = m;
+  else
+    g_batch_err = m;
+  return code;
+}
+
+#define GID_BTRY(b, call)                                                                          \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess) return bfail((b), GID_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+extern "C" void gid_batch_destroy(gid_batch* b) {
+  if (!b) return;
+  for (auto* c : b->ctx) {
+    if (!c) continue;
+    cudaStreamSynchronize(c->stream);
+    gid_destroy(c);
+  }
+  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto s : b->streams) cudaStreamDestroy(s);
+  for (auto e : b->ev_join) cudaEventDestroy(e);
+  if (b->bs) cudaStreamDestroy(b->bs);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  delete b;
+}
+
+extern "C" int gid_batch_create(int n, const int* H, const int* W, const int* K, const gid_weights* w, int per_video,
+                                void* stream, gid_batch** out) {
+  if (!out || n < 1 || !H || !W || !K) return bfail(nullptr, GID_ERR_INVALID_ARG, "bad arguments");
+  *out = nullptr;
+  gid_batch* b = new (std::nothrow) gid_batch();
+  if (!b) return bfail(nullptr, GID_ERR_OOM, "host allocation");
+  b->n = n;
+  b->user = (cudaStream_t)stream;
+  b->ctx.assign(n, nullptr);
+  auto bail = [&](int rc, const std::string& m) {
+    gid_batch_destroy(b);
+    return bfail(nullptr, rc, m);
+  };
+  if (cudaStreamCreateWithFlags(&b->bs, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming) != cudaSuccess)
+    return bail(GID_ERR_CUDA, "batch stream / events");
+  for (int i = 0; i < n; i++) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return bail(GID_ERR_CUDA, "stream");
+    b->streams.push_back(s);
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return bail(GID_ERR_CUDA, "event");
+    b->ev_join.push_back(e);
+    int rc = gid_create(H[i], W[i], K[i], w ? (per_video ? &w[i] : w) : nullptr, s, &b->ctx[i]);
+    if (rc) return bail(rc, std::string("video ") + std::to_string(i) + ": " + gid_last_error(nullptr));
+  }
+  *out = b;
+  return GID_OK;
+}
+
+extern "C" const char* gid_batch_last_error(const gid_batch* b) { return b ? b->err.c_str() : g_batch_err.c_str(); }
+
+extern "C" gid_ctx* gid_batch_ctx(gid_batch* b, int i) { return (b && i >= 0 && i < b->n) ? b->ctx[i] : nullptr; }
+
+// Order the video streams after the caller's stream (before per-video work).
+static int batch_fence_in(gid_batch* b) {
+  GID_BTRY(b, cudaEventRecord(b->ev_in, b->user));
+  for (int i = 0; i < b->n; i++) GID_BTRY(b, cudaStreamWaitEvent(b->streams[i], b->ev_in, 0));
+  return GID_OK;
+}
+
+// Order the caller's stream after every video stream.
+static int batch_fence_out(gid_batch* b) {
+  for (int i = 0; i < b->n; i++) {
+    GID_BTRY(b, cudaEventRecord(b->ev_join[i], b->streams[i]));
+    GID_BTRY(b, cudaStreamWaitEvent(b->user, b->ev_join[i], 0));
+  }
+  return GID_OK;
+}
+
+extern "C" int gid_batch_set_frames(gid_batch* b, const float* const* rgb_dev, const uint8_t* const* labels_dev) {
+  if (!b || !rgb_dev || !labels_dev) return bfail(b, GID_ERR_INVALID_ARG, "NULL argument");
+  if (int rc = batch_fence_in(b)) return rc;
+  for (int i = 0; i < b->n; i++)
+    if (int rc = gid_set_frame(b->ctx[i], rgb_dev[i], labels_dev[i]))
+      return bfail(b, rc, std::string("video ") + std::to_string(i) + ": " + gid_last_error(b->ctx[i]));
+  return batch_fence_out(b);
+}
+
+extern "C" int gid_batch_init(gid_batch* b, int mode) {
+  if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
+  if (int rc = batch_fence_in(b)) return rc;
+  for (int i = 0; i < b->n; i++)
+    if (int rc = gid_init(b->ctx[i], mode))
+      return bfail(b, rc, std::string("video ") + std::to_string(i) + ": " + gid_last_error(b->ctx[i]));
+  return batch_fence_out(b);
+}
+
+extern "C" int gid_batch_new_sequence(gid_batch* b) {
+  if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
+  if (int rc = batch_fence_in(b)) return rc;
+  for (int i = 0; i < b->n; i++)
+    if (int rc = gid_new_sequence(b->ctx[i])) return bfail(b, rc, gid_last_error(b->ctx[i]));
+  return batch_fence_out(b);
+}
+
+// One graph per batch configuration: every video's run is a branch forked from
+// and joined to the batch stream, so the whole frame-step of all videos is one
+// graph launch and the videos' kernels run concurrently.
+extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
+  if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
+  if (n_outer < 1 || m_inner < 1) return bfail(b, GID_ERR_INVALID_ARG, "n_outer >= 1 and m_inner >= 1");
+  std::string key = std::to_string(n_outer) + "," + std::to_string(m_inner);
+  std::vector<int> refine(b->n);
+  for (int i = 0; i < b->n; i++) {
+    gid_ctx* c = b->ctx[i];
+    if (!c->has_frame || !c->initialised) return bfail(b, GID_ERR_STATE, "gid_batch_run before frames / init");
+    c->persistent = false;  // concurrent cooperative grids could not all be co-resident
+    refine[i] = c->w.refine_base_colors == 1 || (c->w.refine_base_colors == 2 && c->frames_solved == 0);
+    key += ";" + std::to_string(refine[i]) + std::to_string((int)c->temporal_active) + std::to_string(c->apply_th);
+  }
+  gid_batch::Graph* g = nullptr;
+  for (auto& e : b->graphs)
+    if (e.key == key) g = &e;
+  if (!g) {
+    long long kernels = 0;
+    GID_BTRY(b, cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
+    int rc = GID_OK;
+    if (cudaEventRecord(b->ev_in, b->bs) != cudaSuccess) rc = GID_ERR_CUDA;
+    for (int i = 0; i < b->n && !rc; i++) {
+      gid_ctx* c = b->ctx[i];
+      if (cudaStreamWaitEvent(b->streams[i], b->ev_in, 0) != cudaSuccess) {
+        rc = GID_ERR_CUDA;
+        break;
+      }
+      const long long l0 = c->launches;
+      rc = enqueue_run(c, n_outer, m_inner, refine[i]);
+      kernels += c->launches - l0;
+      c->launches = l0;
+      if (!rc && (cudaEventRecord(b->ev_join[i], b->streams[i]) != cudaSuccess ||
+                  cudaStreamWaitEvent(b->bs, b->ev_join[i], 0) != cudaSuccess))
+        rc = GID_ERR_CUDA;
+    }
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(b->bs, &graph);
+    if (rc || e != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      return bfail(b, rc ? rc : GID_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
+    }
+    cudaGraphExec_t exec = nullptr;
+    e = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return bfail(b, GID_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    b->graphs.push_back({key, exec, kernels});
+    g = &b->graphs.back();
+  }
+  // replay after everything already queued for the videos and the caller
+  for (int i = 0; i < b->n; i++) {
+    GID_BTRY(b, cudaEventRecord(b->ev_join[i], b->streams[i]));
+    GID_BTRY(b, cudaStreamWaitEvent(b->bs, b->ev_join[i], 0));
+  }
+  GID_BTRY(b, cudaEventRecord(b->ev_in, b->user));
+  GID_BTRY(b, cudaStreamWaitEvent(b->bs, b->ev_in, 0));
+  GID_BTRY(b, cudaGraphLaunch(g->exec, b->bs));
+  GID_BTRY(b, cudaEventRecord(b->ev_out, b->bs));
+  GID_BTRY(b, cudaStreamWaitEvent(b->user, b->ev_out, 0));
+  for (int i = 0; i < b->n; i++) GID_BTRY(b, cudaStreamWaitEvent(b->streams[i], b->ev_out, 0));
+  long long per_video = g->kernels / b->n;  // bookkeeping only: split the count evenly
+  for (int i = 0; i < b->n; i++) {
+    b->ctx[i]->launches += (i == 0) ? g->kernels - per_video * (b->n - 1) : per_video;
+    b->ctx[i]->frames_solved++;
+  }
+  return GID_OK;
+}
+
+// Tile-shape cache: one line "H W K rows" per frame shape.
+static void read_tile_cache(const char* path, std::vector<std::array<int, 4>>& rows) {
+  FILE* f = path ? fopen(path, "r") : nullptr;
+  if (!f) return;
+  std::array<int, 4> r;
+  while (fscanf(f, "%d %d %d %d", &r[0], &r[1], &r[2], &r[3]) == 4) rows.push_back(r);
+  fclose(f);
+}
+
+extern "C" int gid_batch_autotune(gid_batch* b, const char* cache_path, int reps) {
+  if (!b || reps < 1) return bfail(b, GID_ERR_INVALID_ARG, "bad argument");
+  std::vector<std::array<int, 4>> cache;
+  read_tile_cache(cache_path, cache);
+  bool dirty = false;
+  for (int i = 0; i < b->n; i++) {
+    gid_ctx* c = b->ctx[i];
+    int rows = -1;
+    for (auto& r : cache)
+      if (r[0] == c->H && r[1] == c->W && r[2] == c->K) rows = r[3];
+    if (rows < 0) {
+      float us[5];
+      if (int rc = gid_autotune(c, reps, &rows, us)) return bfail(b, rc, gid_last_error(c));
+      if (rows == 0) {  // batches run the multi-kernel PCG: keep its fastest tile shape
+        const int cand[4] = {2, 4, 8, 17};
+        int jb = 0;
+        for (int j = 1; j < 4; j++)
+          if (us[j] < us[jb]) jb = j;
+        rows = cand[jb];
+      }
+      cache.push_back({c->H, c->W, c->K, rows});
+      dirty = true;
+    }
+    if (int rc = gid_set_apply_tile(c, rows)) return bfail(b, rc, gid_last_error(c));
+  }
+  if (dirty && cache_path) {
+    FILE* f = fopen(cache_path, "w");
+    if (!f) return bfail(b, GID_ERR_INVALID_ARG, std::string("cannot write ") + cache_path);
+    for (auto& r : cache) fprintf(f, "%d %d %d %d\n", r[0], r[1], r[2], r[3]);
+    fclose(f);
+  }
   return GID_OK;
 }

@@ -30,7 +30,8 @@ EXPORTS = (
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
-    "gid_set_graphs",
+    "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
+    "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
 )
 
 
@@ -96,8 +97,22 @@ def load():
     L.gid_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), F]
     L.gid_dense_refine_noalloc.argtypes = [I, I, I, P, P, F, ctypes.POINTER(Weights), P, P, P, P,
                                            ctypes.c_char_p, I]
+    L.gid_batch_create.argtypes = [I, ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(I), ctypes.POINTER(Weights),
+                                    I, P, ctypes.POINTER(P)]
+    L.gid_batch_destroy.argtypes = [P]
+    L.gid_batch_destroy.restype = None
+    L.gid_batch_last_error.argtypes = [P]
+    L.gid_batch_last_error.restype = ctypes.c_char_p
+    L.gid_batch_ctx.argtypes = [P, I]
+    L.gid_batch_ctx.restype = P
+    L.gid_batch_set_frames.argtypes = [P, ctypes.POINTER(P), ctypes.POINTER(P)]
+    L.gid_batch_init.argtypes = [P, I]
+    L.gid_batch_new_sequence.argtypes = [P]
+    L.gid_batch_run.argtypes = [P, I, I]
+    L.gid_batch_autotune.argtypes = [P, ctypes.c_char_p, I]
     for n in EXPORTS:
-        if n not in ("gid_default_weights", "gid_destroy", "gid_last_error"):
+        if n not in ("gid_default_weights", "gid_destroy", "gid_last_error", "gid_batch_destroy",
+                     "gid_batch_last_error", "gid_batch_ctx"):
             getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -302,3 +317,103 @@ class Solver:
         n = (ctypes.c_longlong * len(KINDS))()
         self._chk(self.lib.gid_profile_read(self.h, ms, n))
         return {k: (ms[i], n[i]) for i, k in enumerate(KINDS)}
+
+
+class _BatchMember(Solver):
+    """View of one video's context inside a Batch (owned by the batch)."""
+
+    def __init__(self, handle, H, W, K, weights):
+        import torch
+        self.torch = torch
+        self.H, self.W, self.K, self.V = H, W, K, K + 4
+        self.lib = load()
+        self.weights = weights
+        self.h = ctypes.c_void_p(handle)
+
+    def close(self):
+        self.h = None  # the batch owns the context
+
+    # A member context runs on its video's own stream: calls that exchange
+    # device tensors with torch synchronise the device around the call.
+    def _synced(name):
+        def call(self, *a, **k):
+            self.torch.cuda.synchronize()
+            out = getattr(Solver, name)(self, *a, **k)
+            self.torch.cuda.synchronize()
+            return out
+        call.__name__ = name
+        return call
+
+    state = _synced("state")
+    set_state = _synced("set_state")
+    layers = _synced("layers")
+    set_frame = _synced("set_frame")
+    stage_precompute = _synced("stage_precompute")
+    stage_linearize = _synced("stage_linearize")
+    stage_apply = _synced("stage_apply")
+    stage_pcg = _synced("stage_pcg")
+    del _synced
+
+
+class Batch:
+    """n videos of uneven size solved together: one CUDA graph launch per gid_batch_run."""
+
+    def __init__(self, shapes, weights=None, stream=None):
+        """shapes: list of (H, W, K); weights: one Weights or a list of n."""
+        import torch
+        self.lib = load()
+        n = len(shapes)
+        self.shapes = [tuple(s) for s in shapes]
+        Hs = (ctypes.c_int * n)(*[s[0] for s in shapes])
+        Ws = (ctypes.c_int * n)(*[s[1] for s in shapes])
+        Ks = (ctypes.c_int * n)(*[s[2] for s in shapes])
+        per_video = isinstance(weights, (list, tuple))
+        if per_video:
+            warr = (Weights * n)(*weights)
+            wp = ctypes.cast(warr, ctypes.POINTER(Weights))
+            self._w = warr
+        else:
+            self._w = weights if weights is not None else default_weights()
+            wp = ctypes.pointer(self._w)
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.gid_batch_create(n, Hs, Ws, Ks, wp, 1 if per_video else 0, s, ctypes.byref(h))
+        if rc != GID_OK:
+            raise GidError(rc, self.lib.gid_batch_last_error(None).decode())
+        self.h = h
+        self.videos = [_BatchMember(self.lib.gid_batch_ctx(h, i), *self.shapes[i],
+                                    warr[i] if per_video else self._w) for i in range(n)]
+
+    def _chk(self, rc):
+        if rc != GID_OK:
+            raise GidError(rc, self.lib.gid_batch_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.videos = []
+            self.lib.gid_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_frames(self, rgbs, labels):
+        n = len(self.shapes)
+        r = (ctypes.c_void_p * n)(*[t.data_ptr() for t in rgbs])
+        l = (ctypes.c_void_p * n)(*[t.data_ptr() for t in labels])
+        self._chk(self.lib.gid_batch_set_frames(self.h, r, l))
+
+    def init(self, mode=0):
+        self._chk(self.lib.gid_batch_init(self.h, mode))
+
+    def new_sequence(self):
+        self._chk(self.lib.gid_batch_new_sequence(self.h))
+
+    def run(self, n_outer, m_inner):
+        self._chk(self.lib.gid_batch_run(self.h, n_outer, m_inner))
+
+    def autotune(self, cache_path=None, reps=5):
+        self._chk(self.lib.gid_batch_autotune(self.h, cache_path.encode() if cache_path else None, reps))

@@ -57,15 +57,10 @@ def _grid(H: int, W: int):
 
 def voronoi_labels(H: int, W: int, sites: np.ndarray, cell_label: np.ndarray) -> np.ndarray:
     """Label of the nearest site (sites are (n, 2) float pixel positions y, x)."""
+    from scipy.spatial import cKDTree
     yy, xx = np.meshgrid(np.arange(H) + 0.5, np.arange(W) + 0.5, indexing="ij")
-    best = np.full((H, W), np.inf)
-    lab = np.zeros((H, W), np.uint8)
-    for i, (sy, sx) in enumerate(sites):
-        d = (yy - sy) ** 2 + (xx - sx) ** 2
-        m = d < best
-        best[m] = d[m]
-        lab[m] = cell_label[i]
-    return lab
+    _, nearest = cKDTree(np.asarray(sites, np.float64)).query(np.stack([yy.ravel(), xx.ravel()], axis=1))
+    return np.asarray(cell_label, np.uint8)[nearest].reshape(H, W)
 
 
 def direct_shading(H: int, W: int, coef: np.ndarray, theta: float) -> np.ndarray:
