@@ -231,6 +231,80 @@ int gid_batch_run(gid_batch* batch, int n_outer, int m_inner);
  * (cache_path may be NULL: no cache).  Needs frames and states.  Synchronises. */
 int gid_batch_autotune(gid_batch* batch, const char* cache_path, int reps);
 
+/* ---- learned initial state (BF16 encoder-decoder) ---- */
+
+/* The paper has no network; Sec. 8 names learned priors as future work.  This
+ * one predicts the initial state of a frame's solve so that fewer Gauss-Newton
+ * steps reach a given energy.  Architecture (widths w1..w4, default 32, 64, 96,
+ * 128): input 16 channels (the frame I in 0..2, R_cluster = b_init[label] in
+ * 3..5, the cold-start shading estimate mean_c I / mean_c R_cluster in 6, the
+ * one-hot label in 7..7+K-1, zeros); encoder levels 1..4, each two 3x3 convolutions with ReLU, a 2x2
+ * average pool before levels 2..4; decoder levels 3, 2, 1, each a nearest 2x
+ * upsampling of the level below concatenated (first) with the encoder output
+ * of the level, then two 3x3 convolutions with ReLU; a 1x1 head to 2K + 1
+ * channels: K logits w, T_0, T_1..T_K.  Outputs r = ln sum_k softmax(w)_k b_k
+ * (the frame's K x 3 palette b, index-aligned with the solver's base colours)
+ * and T = softplus(T_0..T_K) = ln(1 + exp(.)) (non-negative layers).  Loss: mean squared error of r over B x 3 x H x W values plus that of
+ * T over B x (K+1) x H x W values.  Weights: FP32 masters, BF16 copies for the
+ * tensor-core convolutions (FP32 accumulation), BF16 activations.
+ * Weight blob (host float32, gid_net_num_params values): per layer in the
+ * order e1a e1b e2a e2b e3a e3b e4a e4b d3a d3b d2a d2b d1a d1b head, the
+ * weights as (C_out, C_in, k, k) then the biases (C_out). */
+typedef struct gid_net gid_net;
+
+/* Create a network for K base colours (1..9: the input holds 7 + K channels of
+ * 16); widths: 4 ints, each a
+ * multiple of 32 in [32, 256], or NULL for the defaults.  Weights He-normal
+ * from seed (splitmix64 + Box-Muller), biases zero.  stream: cudaStream_t or
+ * NULL; every call below runs on it.  Synchronises. */
+int gid_net_create(int K, const int* widths, uint64_t seed, void* stream, gid_net** out);
+void gid_net_destroy(gid_net* net);
+const char* gid_net_last_error(const gid_net* net);
+long gid_net_num_params(const gid_net* net);
+long long gid_net_launch_count(const gid_net* net);
+
+/* Weights (and gradients of the last gid_net_backward) as a blob, host.
+ * Setting weights resets the Adam moments.  Synchronise. */
+int gid_net_set_weights(gid_net* net, const float* blob_host);
+int gid_net_get_weights(gid_net* net, float* blob_host);
+int gid_net_get_grads(gid_net* net, float* blob_host);
+
+/* Inference on B frames of H x W (H, W multiples of 8): rgb_dev B x 3 x H x W
+ * float32, labels_dev B x H x W uint8 (>= K read as 0), palette_dev B x K x 3
+ * float32 (> 0), all device.  Writes r_dev (B x 3 x H x W) and T_dev
+ * (B x (K+1) x H x W); either may be NULL.  The activation buffers grow on
+ * demand (a device allocation when a larger batch is first seen).  Async. */
+int gid_net_forward(gid_net* net, int B, int H, int W, const float* rgb_dev, const uint8_t* labels_dev,
+                    const float* palette_dev, float* r_dev, float* T_dev);
+
+/* Forward pass, loss against the targets r_target_dev (B x 3 x H x W) and
+ * T_target_dev (B x (K+1) x H x W), and the gradient of the loss with respect
+ * to every weight (kept in the network for gid_net_adam_step / get_grads).
+ * loss_host: if not NULL, the loss (FP64 sum of FP64 block partials) -- this
+ * synchronises; NULL keeps the call asynchronous. */
+int gid_net_backward(gid_net* net, int B, int H, int W, const float* rgb_dev, const uint8_t* labels_dev,
+                     const float* palette_dev, const float* r_target_dev, const float* T_target_dev,
+                     double* loss_host);
+
+/* Weights of the loss's three parts: the r error, the T_0 error and the
+ * T_1..T_K error (each a mean over its values as above); default 1, 1, 1.
+ * Finite and >= 0, else GID_ERR_INVALID_ARG. */
+int gid_net_set_loss_weights(gid_net* net, float w_r, float w_T0, float w_Tk);
+
+/* One Adam step (Kingma and Ba 2015, bias-corrected) on the FP32 masters with
+ * the last gradients; repacks the BF16 copies.  Async. */
+int gid_net_adam_step(gid_net* net, float lr, float beta1, float beta2, float eps);
+
+/* Learned initial state for the context's current frame: the network's r and
+ * T (palette = the initial base colours) become the state, indirect values
+ * T_1..T_K below the weights' eps written as exactly 0 (the i-sparsity prior's
+ * default; the IRLS weights of Sec. 5.3 hold exact zeros, while a strictly
+ * positive start has non-negativity weight 0 and overshoots), then, when base
+ * colours are refined, one base-colour step (eq:basecolorrefinement) on those
+ * layers.  Needs gid_set_base_colors and gid_set_frame, the same K, and H, W
+ * multiples of 8.  Runs on the context stream.  Async. */
+int gid_init_learned(gid_ctx* ctx, gid_net* net);
+
 /* ---- instrumentation ---- */
 
 /* Kernel kinds for gid_profile_read. */

@@ -6,16 +6,21 @@ plain FP64 definition of the one the CUDA library trains, so that its forward
 pass, loss and every gradient can be checked element by element.
 
 Network (NCHW here, float64):
-  input  x = concat(I (3 channels), R_cluster (3 channels)), zero-padded to 16
+  input  x = concat(I (3 channels), R_cluster (3 channels), the cold-start
+           shading estimate mean_c I / mean_c R_cluster (1 channel), one-hot
+           of the cluster label (K channels)), zero-padded to 16 (K <= 9)
   encoder  level l = 1..4 (widths 32, 64, 96, 128): two 3x3 conv + ReLU; a 2x2
            average pool before levels 2..4
   decoder  levels 3, 2, 1: nearest 2x upsampling, concatenation with the
            encoder output of that level, two 3x3 conv + ReLU
   head     1x1 conv to 2K + 1 channels: K reflectance logits w, T_0, T_1..T_K
   output   R_c = sum_k softmax(w)_k b_kc (b the frame's K x 3 palette),
-           r = ln R, T = (T_0..T_K)
+           r = ln R, T = softplus(T_0..T_K) = ln(1 + exp(.)): the layers are
+           non-negative (the non-negativity term of Sec. 5.3); a smooth map
+           keeps a gradient where a clip at zero would not
 Loss: mean squared error of r over B x 3 x H x W values plus mean squared error
-of T over B x (K + 1) x H x W values.
+of T over B x (K + 1) x H x W values, with optional factors on the r part, the
+T_0 part and the T_1..T_K part.
 
 Weights blob (float32 or float64, flat): for every conv layer in order, W with
 shape (C_out, C_in, k, k) then bias (C_out,).
@@ -127,14 +132,29 @@ def relu(x):
     return np.maximum(x, 0.0)
 
 
+def softplus(x):
+    return np.logaddexp(0.0, x)
+
+
+def sigmoid(x):
+    return 0.5 * (1.0 + np.tanh(0.5 * x))
+
+
 # ---------------------------------------------------------------- network
 
-def make_input(rgb, rcl):
-    """(B, 3, H, W) image and clustered reflectance -> (B, 16, H, W)."""
+def make_input(rgb, rcl, labels=None, K=0):
+    """(B, 3, H, W) image, clustered reflectance and (B, H, W) labels in 0..K-1
+    -> (B, 16, H, W).  The softmax logits of the head index the palette, so the
+    label itself (one-hot) is part of the input."""
     B, _, H, W = rgb.shape
+    assert 7 + K <= IN_PAD
     x = np.zeros((B, IN_PAD, H, W))
     x[:, 0:3] = rgb
     x[:, 3:6] = rcl
+    x[:, 6] = rgb.mean(axis=1) / rcl.mean(axis=1)
+    if labels is not None:
+        for k in range(K):
+            x[:, 7 + k] = labels == k
     return x
 
 
@@ -167,22 +187,25 @@ def forward(params, x, palette, K):
     s = e / e.sum(axis=1, keepdims=True)                       # (B, K, H, W)
     R = np.einsum("bkhw,bkc->bchw", s, palette)                 # (B, 3, H, W)
     c["head_out"] = (s, R)
-    return np.log(R), h[:, K:], c
+    return np.log(R), softplus(h[:, K:]), c
 
 
-def loss_and_grads(params, x, palette, K, r_tgt, T_tgt):
-    """L and dL/dparams (same dict layout), and dL/dx."""
+def loss_and_grads(params, x, palette, K, r_tgt, T_tgt, weights=(1.0, 1.0, 1.0)):
+    """L and dL/dparams (same dict layout), and dL/dx.  weights: the factors of
+    the r part, the T_0 part and the T_1..T_K part of the loss."""
     r, T, c = forward(params, x, palette, K)
     nr, nT = r.size, T.size
-    L = np.sum((r - r_tgt) ** 2) / nr + np.sum((T - T_tgt) ** 2) / nT
-    gr = 2.0 * (r - r_tgt) / nr
-    gT = 2.0 * (T - T_tgt) / nT
+    wT = np.full((1, K + 1, 1, 1), float(weights[2]))
+    wT[0, 0] = weights[1]
+    L = weights[0] * np.sum((r - r_tgt) ** 2) / nr + np.sum(wT * (T - T_tgt) ** 2) / nT
+    gr = weights[0] * 2.0 * (r - r_tgt) / nr
+    gT = wT * 2.0 * (T - T_tgt) / nT
     s, R = c["head_out"]
     gR = gr / R                                                  # d ln R / dR
     # R_c = sum_j s_j b_jc ; ds_k/dw_l = s_k (delta_kl - s_l)
     gs = np.einsum("bchw,bkc->bkhw", gR, palette)
     gw = s * (gs - np.sum(gs * s, axis=1, keepdims=True))
-    gh = np.concatenate([gw, gT], axis=1)
+    gh = np.concatenate([gw, gT * sigmoid(c["head"][1][:, K:])], axis=1)
     grads = {}
     d1, _ = c["head"]
     g, dW, db = conv_backward(d1, params["head"][0], gh)

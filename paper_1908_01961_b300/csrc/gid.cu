@@ -5,6 +5,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -13,6 +14,7 @@
 
 #include "../../include/gid.h"
 #include "gid_kernels.cuh"
+#include "gid_net_internal.h"
 
 using namespace gid;
 
@@ -502,6 +504,31 @@ extern "C" int gid_init(gid_ctx* c, int mode) {
     if (!c->initialised) return fail(c, GID_ERR_STATE, "warm start needs a previous state");
   } else {
     return fail(c, GID_ERR_INVALID_ARG, "init mode must be 0 (cold) or 1 (warm)");
+  }
+  c->initialised = true;
+  return GID_OK;
+}
+
+extern "C" int gid_init_learned(gid_ctx* c, gid_net* net) {
+  if (!c || !net) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (!c->has_frame || !c->has_colors)
+    return fail(c, GID_ERR_STATE, "gid_init_learned needs gid_set_base_colors and gid_set_frame");
+  if (gidnet_K(net) != c->K) return fail(c, GID_ERR_INVALID_ARG, "network and context have different K");
+  if (c->H % 8 || c->W % 8) return fail(c, GID_ERR_INVALID_ARG, "learned start needs H and W multiples of 8");
+  // the palette is the initial (clustered) base colours, index-aligned with b_1..b_K
+  const float* palette = reinterpret_cast<const float*>(reinterpret_cast<const char*>(c->col) +
+                                                        offsetof(DevColors, binit));
+  std::string msg;
+  // Indirect values below the IRLS epsilon start at exactly zero: the sparse
+  // prior's default state, which the reweighting of Sec. 5.3 keeps from
+  // overshooting below zero (a strictly positive start has non-negativity
+  // weight zero everywhere).
+  if (int rc = gidnet_infer_planes(net, c->H, c->W, c->I, c->plane, c->pitch, c->lab, palette, c->w.eps, c->X,
+                                   c->stream, &c->launches, &msg))
+    return fail(c, rc, "network forward", msg.c_str());
+  if (c->w.refine_base_colors != 0) {
+    launch(c, GID_KIND_DENSE, [&] { GID_DISPATCH(c, dense, c, 1); });
+    if (int rc = check_launch(c, "k_dense")) return rc;
   }
   c->initialised = true;
   return GID_OK;

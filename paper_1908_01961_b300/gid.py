@@ -32,6 +32,9 @@ EXPORTS = (
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
     "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
+    "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
+    "gid_net_set_weights", "gid_net_get_weights", "gid_net_get_grads", "gid_net_forward", "gid_net_backward",
+    "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned",
 )
 
 
@@ -110,9 +113,27 @@ def load():
     L.gid_batch_new_sequence.argtypes = [P]
     L.gid_batch_run.argtypes = [P, I, I]
     L.gid_batch_autotune.argtypes = [P, ctypes.c_char_p, I]
+    L.gid_net_create.argtypes = [I, ctypes.POINTER(I), ctypes.c_uint64, P, ctypes.POINTER(P)]
+    L.gid_net_destroy.argtypes = [P]
+    L.gid_net_destroy.restype = None
+    L.gid_net_last_error.argtypes = [P]
+    L.gid_net_last_error.restype = ctypes.c_char_p
+    L.gid_net_num_params.argtypes = [P]
+    L.gid_net_num_params.restype = ctypes.c_long
+    L.gid_net_launch_count.argtypes = [P]
+    L.gid_net_launch_count.restype = ctypes.c_longlong
+    L.gid_net_set_weights.argtypes = [P, F]
+    L.gid_net_get_weights.argtypes = [P, F]
+    L.gid_net_get_grads.argtypes = [P, F]
+    L.gid_net_forward.argtypes = [P, I, I, I, P, P, P, P, P]
+    L.gid_net_backward.argtypes = [P, I, I, I, P, P, P, P, P, D]
+    L.gid_net_adam_step.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.gid_net_set_loss_weights.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float]
+    L.gid_init_learned.argtypes = [P, P]
     for n in EXPORTS:
         if n not in ("gid_default_weights", "gid_destroy", "gid_last_error", "gid_batch_destroy",
-                     "gid_batch_last_error", "gid_batch_ctx"):
+                     "gid_batch_last_error", "gid_batch_ctx", "gid_net_destroy", "gid_net_last_error",
+                     "gid_net_num_params", "gid_net_launch_count"):
             getattr(L, n).restype = ctypes.c_int
     _lib = L
     return L
@@ -223,6 +244,10 @@ class Solver:
 
     def init(self, mode: int = 0):
         self._chk(self.lib.gid_init(self.h, mode))
+
+    def init_learned(self, net: "Net"):
+        """Initial state from the warm-start network (gid_init_learned)."""
+        self._chk(self.lib.gid_init_learned(self.h, net.h))
 
     def run(self, n_outer: int, m_inner: int):
         self._chk(self.lib.gid_run(self.h, n_outer, m_inner))
@@ -417,3 +442,94 @@ class Batch:
 
     def autotune(self, cache_path=None, reps=5):
         self._chk(self.lib.gid_batch_autotune(self.h, cache_path.encode() if cache_path else None, reps))
+
+
+class Net:
+    """One gid_net: the warm-start encoder-decoder for K base colours (include/gid.h)."""
+
+    def __init__(self, K: int, widths=(32, 64, 96, 128), seed: int = 0, stream=None):
+        import torch
+        self.torch = torch
+        self.K = K
+        self.widths = tuple(int(w) for w in widths)
+        self.lib = load()
+        wd = (ctypes.c_int * 4)(*self.widths)
+        s = ctypes.c_void_p(stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream)
+        h = ctypes.c_void_p()
+        rc = self.lib.gid_net_create(K, wd, ctypes.c_uint64(seed), s, ctypes.byref(h))
+        if rc != GID_OK:
+            raise GidError(rc, self.lib.gid_net_last_error(None).decode())
+        self.h = h
+        self.n_params = int(self.lib.gid_net_num_params(h))
+
+    def _chk(self, rc):
+        if rc != GID_OK:
+            raise GidError(rc, self.lib.gid_net_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.gid_net_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_weights(self, blob):
+        b = np.ascontiguousarray(blob, dtype=np.float32).ravel()
+        assert b.size == self.n_params, (b.size, self.n_params)
+        self._chk(self.lib.gid_net_set_weights(self.h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+
+    def weights(self) -> np.ndarray:
+        b = np.zeros(self.n_params, np.float32)
+        self._chk(self.lib.gid_net_get_weights(self.h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return b
+
+    def grads(self) -> np.ndarray:
+        b = np.zeros(self.n_params, np.float32)
+        self._chk(self.lib.gid_net_get_grads(self.h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return b
+
+    def launch_count(self) -> int:
+        return int(self.lib.gid_net_launch_count(self.h))
+
+    def _inputs(self, rgb, labels, palette):
+        t = self.torch
+        B, C, H, W = rgb.shape
+        for x, shape, dt in ((rgb, (B, 3, H, W), t.float32), (labels, (B, H, W), t.uint8),
+                             (palette, (B, self.K, 3), t.float32)):
+            assert x.is_cuda and x.is_contiguous() and tuple(x.shape) == shape and x.dtype == dt, (x.shape, shape)
+        return B, H, W
+
+    def forward(self, rgb, labels, palette, r=None, T=None):
+        """rgb (B, 3, H, W), labels (B, H, W) uint8, palette (B, K, 3): CUDA tensors.
+        Returns (r, T) = ((B, 3, H, W), (B, K+1, H, W)) float32 CUDA tensors."""
+        t = self.torch
+        B, H, W = self._inputs(rgb, labels, palette)
+        r = t.empty((B, 3, H, W), device="cuda") if r is None else r
+        T = t.empty((B, self.K + 1, H, W), device="cuda") if T is None else T
+        self._chk(self.lib.gid_net_forward(self.h, B, H, W, _ptr(rgb), _ptr(labels), _ptr(palette), _ptr(r), _ptr(T)))
+        return r, T
+
+    def backward(self, rgb, labels, palette, r_target, T_target, sync_loss: bool = True):
+        """Loss and weight gradients (kept in the network); returns the loss or None."""
+        B, H, W = self._inputs(rgb, labels, palette)
+        assert tuple(r_target.shape) == (B, 3, H, W) and tuple(T_target.shape) == (B, self.K + 1, H, W)
+        assert r_target.is_contiguous() and T_target.is_contiguous()
+        loss = ctypes.c_double()
+        self._chk(self.lib.gid_net_backward(self.h, B, H, W, _ptr(rgb), _ptr(labels), _ptr(palette), _ptr(r_target),
+                                            _ptr(T_target), ctypes.byref(loss) if sync_loss else None))
+        return loss.value if sync_loss else None
+
+    def set_loss_weights(self, w_r: float = 1.0, w_T0: float = 1.0, w_Tk: float = 1.0):
+        self._chk(self.lib.gid_net_set_loss_weights(self.h, w_r, w_T0, w_Tk))
+
+    def adam_step(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self._chk(self.lib.gid_net_adam_step(self.h, lr, beta1, beta2, eps))
+
+    def train_step(self, rgb, labels, palette, r_target, T_target, lr, sync_loss=False):
+        loss = self.backward(rgb, labels, palette, r_target, T_target, sync_loss)
+        self.adam_step(lr)
+        return loss

@@ -1,0 +1,234 @@
+"""Training and evaluation of the warm-start network (gid_net, include/gid.h).
+
+The network learns to predict, from a frame and its clustered reflectance, the
+decomposition that the plain solver reaches from its cold start (N = 8
+Gauss-Newton steps of M = 20 PCG steps), so that a solve started from the
+prediction needs fewer Gauss-Newton steps to reach the same energy.  The paper
+has no network (Sec. 8 names learned priors as future work); everything here
+runs through the library: the targets come from gid_run, the training from
+gid_net_backward / gid_net_adam_step, the evaluation from gid_init_learned.
+
+Data: seeded synthetic 640 x 480 frames with K = 6 (40 Voronoi cells, the
+workload of the 30-frame video), each solved once; training samples are random
+256 x 256 crops of those frames and of their solved layers.  Evaluation: held-
+out frames (other seeds), each solved from the cold start and from the learned
+start; the learned start's cost is the number of Gauss-Newton steps after
+which its exact energy is at or below the cold start's final energy.
+
+Command line:
+    python -m paper_1908_01961_b300.warmstart train --frames 1000 --steps 6000 --out FILE.npy
+    python -m paper_1908_01961_b300.warmstart evaluate --weights FILE.npy --frames 20
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import time
+
+import numpy as np
+
+from . import gid, synth
+
+H, W, K, N_CELLS, NOISE = 480, 640, 6, 40, 0.01
+N_OUTER, M_INNER = 8, 20
+TRAIN_SEED0, EVAL_SEED0 = 1_000_000, 2_000_000
+WIDTHS = (32, 64, 96, 128)
+# The indirect layers are small (a few hundredths) and sparse; without a larger
+# factor their error hardly registers in the loss and the network predicts
+# them as zero, a state the IRLS weights of Sec. 5.3 leave only slowly.
+LOSS_WEIGHTS = (1.0, 1.0, 10.0)
+HERE = os.path.dirname(os.path.abspath(__file__))
+DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart_K6.npy")
+
+
+def solver_weights():
+    """Solver settings of the single-frame solves: default term weights, the
+    spatial pair offsets of seed 0, no temporal pairs."""
+    off_s, _ = synth.offsets_for(0)
+    return gid.default_weights(off_s)
+
+
+def _make_frame(args):
+    seed, t = args
+    v = synth.SyntheticVideo(H, W, K, N_CELLS, seed=seed, noise=NOISE)
+    f = v.frame(t)
+    b = synth.initial_base_colors(f.I, f.labels, K)
+    return f.I.astype(np.float32), f.labels.astype(np.uint8), b.astype(np.float32)
+
+
+def generate(seeds, workers=None):
+    """Frames (I, labels, b_init) for the given seeds; frame t = seed mod 30 of
+    each seed's video (so the light direction varies as in the video)."""
+    jobs = [(int(s), int(s) % 30) for s in seeds]
+    workers = workers or max(1, min(32, (os.cpu_count() or 2) - 1, len(jobs)))
+    if workers == 1:
+        return [_make_frame(j) for j in jobs]
+    with mp.get_context("spawn").Pool(workers) as pool:
+        return pool.map(_make_frame, jobs, chunksize=max(1, len(jobs) // (4 * workers)))
+
+
+class Dataset:
+    """Frames and their plain-solver layers, resident on the GPU."""
+
+    def __init__(self, frames, n_outer=N_OUTER, m_inner=M_INNER, log=None):
+        import torch
+        n = len(frames)
+        self.n = n
+        self.rgb = torch.empty((n, 3, H, W), device="cuda")
+        self.lab = torch.empty((n, H, W), dtype=torch.uint8, device="cuda")
+        self.pal = torch.empty((n, K, 3), device="cuda")
+        self.r = torch.empty((n, 3, H, W), device="cuda")
+        self.T = torch.empty((n, K + 1, H, W), device="cuda")
+        s = gid.Solver(H, W, K, solver_weights())
+        t0 = time.time()
+        for i, (I, lab, b) in enumerate(frames):
+            self.rgb[i].copy_(torch.from_numpy(I))
+            self.lab[i].copy_(torch.from_numpy(lab))
+            self.pal[i].copy_(torch.from_numpy(b))
+            s.set_base_colors(b)
+            s.set_frame(self.rgb[i], self.lab[i])
+            s.init(0)
+            s.run(n_outer, m_inner)
+            X = s.state()
+            self.r[i].copy_(X[:3])
+            self.T[i].copy_(X[3:])
+            if log and (i + 1) % 200 == 0:
+                log(f"solved {i + 1}/{n} frames ({time.time() - t0:.1f} s)")
+        torch.cuda.synchronize()
+        s.close()
+
+    def crops(self, gen, batch, size):
+        """A batch of random size x size crops (frame and offsets drawn from gen)."""
+        import torch
+        idx = torch.randint(self.n, (batch,), generator=gen).tolist()
+        ys = torch.randint(0, (H - size) // 8 + 1, (batch,), generator=gen).mul(8).tolist()
+        xs = torch.randint(0, (W - size) // 8 + 1, (batch,), generator=gen).mul(8).tolist()
+        def cut(t, i, y, x):
+            return t[i, ..., y:y + size, x:x + size]
+        out = []
+        for t in (self.rgb, self.lab, self.r, self.T):
+            out.append(torch.stack([cut(t, i, y, x) for i, y, x in zip(idx, ys, xs)]).contiguous())
+        pal = self.pal[idx].contiguous()
+        return out[0], out[1], pal, out[2], out[3]
+
+
+def train(net, data, steps, batch=8, size=256, lr=2e-3, lr_min=2e-5, seed=0, log=None, log_every=250):
+    """Adam with a cosine learning-rate decay from lr to lr_min; returns the
+    logged (step, loss) pairs."""
+    import torch
+    gen = torch.Generator().manual_seed(seed)
+    hist = []
+    t0 = time.time()
+    for step in range(steps):
+        a = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(1, steps - 1)))
+        rgb, lab, pal, r, T = data.crops(gen, batch, size)
+        want = step % log_every == 0 or step == steps - 1
+        loss = net.train_step(rgb, lab, pal, r, T, a, sync_loss=want)
+        if want:
+            hist.append((step, loss))
+            if log:
+                log(f"step {step} lr {a:.2e} loss {loss:.5f} ({time.time() - t0:.1f} s)")
+    return hist
+
+
+def energies(solver, n_outer=N_OUTER, m_inner=M_INNER):
+    """Exact energy (total, and per term: rows of 8) after each of n_outer single
+    Gauss-Newton steps; row 0 is the starting state."""
+    tot, per = [], []
+    for i in range(n_outer + 1):
+        if i:
+            solver.run(1, m_inner)
+        t, p = solver.energy()
+        tot.append(t)
+        per.append(p)
+    return np.array(tot), np.array(per)
+
+
+def evaluate(net, frames, n_outer=N_OUTER, m_inner=M_INNER, log=None):
+    """Per frame: energies of the cold and the learned start after 0..n_outer
+    Gauss-Newton steps, and the learned start's step count to reach the cold
+    start's final energy (n_outer + 1 if it never does)."""
+    import torch
+    s = gid.Solver(H, W, K, solver_weights())
+    out = []
+    for i, (I, lab, b) in enumerate(frames):
+        rgb, lb = torch.from_numpy(I).cuda(), torch.from_numpy(lab).cuda()
+        s.set_base_colors(b)
+        s.set_frame(rgb, lb)
+        s.init(0)
+        Ec, Pc = energies(s, n_outer, m_inner)
+        s.set_base_colors(b)
+        s.init_learned(net)
+        El, Pl = energies(s, n_outer, m_inner)
+        hit = np.nonzero(El <= Ec[-1])[0]
+        n_l = int(hit[0]) if len(hit) else n_outer + 1
+        out.append(dict(E_cold=Ec.tolist(), E_learned=El.tolist(), n_learned=n_l,
+                        terms_cold=Pc.tolist(), terms_learned=Pl.tolist()))
+        if log:
+            log(f"frame {i}: cold E {Ec[0]:.4e} -> {Ec[-1]:.4e}; learned E0 {El[0]:.4e}, reaches it after {n_l} steps")
+    s.close()
+    return out
+
+
+def load_net(path=DEFAULT_WEIGHTS, stream=None):
+    net = gid.Net(K, WIDTHS, stream=stream)
+    net.set_weights(np.load(path))
+    return net
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("cmd", choices=("train", "evaluate"))
+    ap.add_argument("--frames", type=int, default=1000)
+    ap.add_argument("--steps", type=int, default=6000)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=2e-3)
+    ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--loss-weights", type=float, nargs=3, default=LOSS_WEIGHTS, metavar=("W_R", "W_T0", "W_TK"))
+    ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--weights", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--eval-frames", type=int, default=10)
+    ap.add_argument("--report", default=None, help="write a JSON summary here")
+    a = ap.parse_args(argv)
+
+    def log(m):
+        print(m, flush=True)
+
+    report = {}
+    if a.cmd == "train":
+        t0 = time.time()
+        frames = generate(range(TRAIN_SEED0, TRAIN_SEED0 + a.frames))
+        log(f"generated {len(frames)} frames in {time.time() - t0:.1f} s")
+        t1 = time.time()
+        data = Dataset(frames, log=log)
+        del frames
+        log(f"plain-solver targets in {time.time() - t1:.1f} s")
+        net = gid.Net(K, WIDTHS, seed=a.seed)
+        net.set_loss_weights(*a.loss_weights)
+        t2 = time.time()
+        hist = train(net, data, a.steps, a.batch, lr=a.lr, seed=a.seed, log=log)
+        report.update(train_frames=a.frames, steps=a.steps, batch=a.batch, crop=256, lr=a.lr,
+                      loss_weights=list(a.loss_weights),
+                      train_seconds=time.time() - t2, loss=hist)
+        os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+        np.save(a.out, net.weights())
+        log(f"saved {a.out}")
+        del data
+    else:
+        net = load_net(a.weights)
+    if a.eval_frames > 0:
+        ev = evaluate(net, generate(range(EVAL_SEED0, EVAL_SEED0 + a.eval_frames)), log=log)
+        n = [e["n_learned"] for e in ev]
+        report.update(eval_frames=a.eval_frames, n_learned=n, n_learned_max=max(n), n_cold=N_OUTER,
+                      mean_ratio=float(np.mean(n)) / N_OUTER, frames=ev)
+        log(f"learned start reaches the cold-start energy after {n} Gauss-Newton steps (cold: {N_OUTER})")
+    if a.report:
+        with open(a.report, "w") as f:
+            json.dump(report, f, indent=1)
+
+
+if __name__ == "__main__":
+    main()

@@ -56,3 +56,15 @@ def test_invalid_sizes_rejected_before_any_device_call():
     assert lib.gid_create(0, 8, 2, None, None, ctypes.byref(h)) == -1
     w = gid.default_weights([[4, 0]])                     # offset beyond the 3-pixel radius
     assert lib.gid_create(8, 8, 2, ctypes.byref(w), None, ctypes.byref(h)) == -1
+
+
+def test_network_create_rejects_bad_arguments_and_missing_device():
+    import torch
+    lib = gid.load()
+    h = ctypes.c_void_p()
+    assert lib.gid_net_create(11, None, 0, None, ctypes.byref(h)) == -1
+    bad = (ctypes.c_int * 4)(32, 48, 96, 128)
+    assert lib.gid_net_create(3, bad, 0, None, ctypes.byref(h)) == -1
+    assert lib.gid_net_num_params(None) == 0
+    if not torch.cuda.is_available():
+        assert lib.gid_net_create(3, None, 0, None, ctypes.byref(h)) == -2 and not h.value

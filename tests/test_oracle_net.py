@@ -49,7 +49,13 @@ def test_head_limits():
     b[1] = 60.0
     r, T, _ = net.forward(params, x, palette, K)
     assert np.allclose(np.exp(r[0, :, 3, 3]), palette[0, 1], rtol=1e-12)
-    assert np.all(T == 0)
+    assert np.allclose(T, np.log(2.0), rtol=1e-14)                  # softplus(0)
+    b[K] = -30.0                                                     # softplus -> exp for large negative
+    _, T, _ = net.forward(params, x, palette, K)
+    assert np.allclose(T[:, 0], np.exp(-30.0), rtol=1e-12)
+    b[K] = 40.0                                                      # and -> identity for large positive
+    _, T, _ = net.forward(params, x, palette, K)
+    assert np.allclose(T[:, 0], 40.0, rtol=1e-15)
 
 
 def _problem(seed=0, K=2, H=8, W=8):
@@ -57,7 +63,8 @@ def _problem(seed=0, K=2, H=8, W=8):
     blob = net.he_init(K, seed, TINY).astype(np.float64)
     blob += rng.normal(0, 0.05, size=blob.shape)          # non-zero biases too
     params = net.unpack(blob, K, TINY)
-    x = net.make_input(rng.uniform(0.1, 0.9, (1, 3, H, W)), rng.uniform(0.1, 0.9, (1, 3, H, W)))
+    x = net.make_input(rng.uniform(0.1, 0.9, (1, 3, H, W)), rng.uniform(0.1, 0.9, (1, 3, H, W)),
+                       rng.integers(0, K, (1, H, W)), K)
     palette = rng.uniform(0.2, 0.8, (1, K, 3))
     r_t = rng.normal(-0.7, 0.2, (1, 3, H, W))
     T_t = rng.normal(0.3, 0.2, (1, K + 1, H, W))
@@ -67,12 +74,13 @@ def _problem(seed=0, K=2, H=8, W=8):
 def test_gradients_match_finite_differences():
     K = 2
     blob, params, x, palette, r_t, T_t = _problem(K=K)
-    L, grads, gx = net.loss_and_grads(params, x, palette, K, r_t, T_t)
+    wts = (0.7, 1.3, 4.0)
+    L, grads, gx = net.loss_and_grads(params, x, palette, K, r_t, T_t, wts)
     gblob = net.pack(grads, K, TINY)
     rng = np.random.default_rng(7)
 
     def loss_at(b):
-        return net.loss_and_grads(net.unpack(b, K, TINY), x, palette, K, r_t, T_t)[0]
+        return net.loss_and_grads(net.unpack(b, K, TINY), x, palette, K, r_t, T_t, wts)[0]
 
     h = 1e-6
     idx = rng.choice(blob.size, size=40, replace=False)
@@ -89,9 +97,35 @@ def test_gradients_match_finite_differences():
     for (c, yy, xx) in [(0, 0, 0), (4, 3, 5), (2, 7, 7)]:
         e = np.zeros_like(x)
         e[0, c, yy, xx] = h
-        fd = (net.loss_and_grads(params, x + e, palette, K, r_t, T_t)[0] -
-              net.loss_and_grads(params, x - e, palette, K, r_t, T_t)[0]) / (2 * h)
+        fd = (net.loss_and_grads(params, x + e, palette, K, r_t, T_t, wts)[0] -
+              net.loss_and_grads(params, x - e, palette, K, r_t, T_t, wts)[0]) / (2 * h)
         assert gx[0, c, yy, xx] == pytest.approx(fd, rel=1e-5, abs=1e-9)
+
+
+def test_input_layout():
+    rgb = np.full((1, 3, 2, 2), 0.5)
+    rcl = np.full((1, 3, 2, 2), 0.25)
+    lab = np.array([[[0, 2], [1, 2]]])
+    x = net.make_input(rgb, rcl, lab, 3)
+    assert np.all(x[:, :3] == 0.5) and np.all(x[:, 3:6] == 0.25) and np.all(x[:, 10:] == 0)
+    assert np.all(x[:, 6] == 2.0)                                   # mean I / mean R_cluster
+    assert np.array_equal(x[0, 7:10].argmax(axis=0), lab[0]) and np.all(x[0, 7:10].sum(axis=0) == 1)
+
+
+def test_loss_weights_scale_each_part():
+    """Weights (a, b, c) give a L_r + b L_T0 + c L_Tk, and the gradients are linear in them."""
+    K = 2
+    blob, params, x, palette, r_t, T_t = _problem(K=K)
+    parts = []
+    for w in ((1, 0, 0), (0, 1, 0), (0, 0, 1)):
+        L, g, _ = net.loss_and_grads(params, x, palette, K, r_t, T_t, w)
+        parts.append((L, net.pack(g, K, TINY)))
+    L, g, _ = net.loss_and_grads(params, x, palette, K, r_t, T_t, (0.5, 2.0, 3.0))
+    assert L == pytest.approx(0.5 * parts[0][0] + 2 * parts[1][0] + 3 * parts[2][0], rel=1e-12)
+    assert np.allclose(net.pack(g, K, TINY), 0.5 * parts[0][1] + 2 * parts[1][1] + 3 * parts[2][1], rtol=1e-9,
+                       atol=1e-15)
+    L1, _, _ = net.loss_and_grads(params, x, palette, K, r_t, T_t)
+    assert L1 == pytest.approx(sum(p[0] for p in parts), rel=1e-12)
 
 
 def test_adam_first_step_is_signed_lr():
