@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=WORK["frames"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--tile", type=int, default=None, choices=[0, 2, 4, 8, 17],
+                    help="operator tile rows instead of autotuning (0 = persistent PCG kernel); for profiling")
     ap.add_argument("--workload", default="video", choices=["video", "batch"],
                     help="video: the 640x480 K=6 video (default); batch: 24 uneven videos in one graph per step")
     return ap.parse_args()
@@ -253,7 +256,11 @@ def run_gid(args, ws, rank, local):
             s.run(N, M)
 
     step()
-    tile_rows, tile_us = s.autotune(10)     # operator tile shape for this frame size (setup, untimed)
+    if args.tile is None:
+        tile_rows, tile_us = s.autotune(10)     # operator tile shape for this frame size (setup, untimed)
+    else:
+        s.set_apply_tile(args.tile)
+        tile_rows, tile_us = args.tile, "fixed by --tile"
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -326,6 +333,10 @@ def run_gid(args, ws, rank, local):
                "h2d_bytes_per_step": F * (3 * P * 4 + P),
                "d2h_bytes_per_step": F * ((3 + K + 1) * P * 4 + K * 3 * 4)}
 
+    learned = None
+    if rank == 0 and not args.no_learned:
+        learned = learned_arm(dev, flush)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
@@ -341,10 +352,79 @@ def run_gid(args, ws, rank, local):
                "config": {"workload": WORKLOAD, "H": H, "W": W, "K": K, "frames_per_step": F, "N_outer": N,
                           "M_inner": M, "l2": "flushed before each step (256 MB write, outside the events)",
                           "parallelism": f"replicas x{ws} (one video per GPU)",
-                          "operator_tile": f"128x{tile_rows} (autotuned; us per PCG step {tile_us})"},
+                          "operator_tile": (f"128x{tile_rows}" if tile_rows else "persistent PCG kernel") +
+                          (f" (autotuned; us per PCG step {tile_us})" if args.tile is None else " (fixed)")},
                "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
-               "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E}
+               "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E,
+               "learned_warm_start": learned}
         print(json.dumps(out), flush=True)
+
+
+# ---------------------------------------------------------------- learned warm start
+
+LEARNED_FRAMES = 3
+LEARNED_REPS = 5
+
+
+def learned_arm(dev, flush):
+    """Frames/s of a single 640x480 K=6 frame solved to the cold start's final
+    energy: plain (cold start, 8 Gauss-Newton steps) against the learned start
+    (network forward, T_0 refit, base-colour step, then as many Gauss-Newton
+    steps as the held-out frames needed to reach that energy).  Step counts from
+    energies after every step on LEARNED_FRAMES held-out frames; times from CUDA
+    events over LEARNED_REPS solves of the first frame (L2 flushed between)."""
+    import torch
+
+    from paper_1908_01961_b300 import gid
+    from paper_1908_01961_b300 import warmstart as WS
+    if not os.path.exists(WS.DEFAULT_WEIGHTS):
+        return {"unavailable": "no trained weights file"}
+    net = WS.load_net()
+    frames = WS.generate(range(WS.EVAL_SEED0, WS.EVAL_SEED0 + LEARNED_FRAMES), workers=1)
+    ev = WS.evaluate(net, frames, zero_below=(WS.ZERO_BELOW,), learned_steps=2 * WS.N_OUTER)
+    n_cold = [int(np.nonzero(np.array(e["E_cold"]) <= e["E_cold"][-1])[0][0]) for e in ev]
+    n_learned = [e["learned"][str(WS.ZERO_BELOW)]["n"] for e in ev]
+    nc, nl = max(n_cold), max(n_learned)
+    I, lab, b = frames[0]
+    rgb, lb = torch.from_numpy(I).to(dev), torch.from_numpy(lab).to(dev)
+    s = gid.Solver(WS.H, WS.W, WS.K, WS.solver_weights())
+    s.set_base_colors(b)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps=LEARNED_REPS):
+        for _ in range(3):
+            fn()
+        out = []
+        for i in range(reps):
+            flush.fill_(float(i))
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            z.record(stream)
+            torch.cuda.synchronize()
+            out.append(a.elapsed_time(z))
+        return statistics.median(out)
+
+    def cold():
+        s.new_sequence()
+        s.set_frame(rgb, lb)
+        s.init(0)
+        s.run(nc, WS.M_INNER)
+
+    def learned(n):
+        s.new_sequence()
+        s.set_frame(rgb, lb)
+        s.init_learned(net, WS.ZERO_BELOW)
+        if n:
+            s.run(n, WS.M_INNER)
+
+    ms_cold, ms_learned, ms_init = timed(cold), timed(lambda: learned(nl)), timed(lambda: learned(0))
+    return {"eval_frames": LEARNED_FRAMES, "eval_seeds": f"{WS.EVAL_SEED0}..{WS.EVAL_SEED0 + LEARNED_FRAMES - 1}",
+            "gn_steps_to_cold_final_energy": {"cold": n_cold, "learned": n_learned},
+            "gn_steps_timed": {"cold": nc, "learned": nl}, "gn_step_ratio": nl / nc,
+            "frames_per_s_cold": 1000.0 / ms_cold, "frames_per_s_learned": 1000.0 / ms_learned,
+            "ms_cold": ms_cold, "ms_learned": ms_learned, "ms_learned_init": ms_init,
+            "zero_below": WS.ZERO_BELOW, "weights": os.path.relpath(WS.DEFAULT_WEIGHTS, ROOT)}
 
 
 # ---------------------------------------------------------------- batched workload

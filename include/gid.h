@@ -136,6 +136,12 @@ int gid_get_layers(gid_ctx* ctx, float* R_dev, float* T_dev);
 int gid_get_state(gid_ctx* ctx, float* X_dev);
 int gid_set_state(gid_ctx* ctx, const float* X_dev);
 
+/* One base-colour step (eq:basecolorrefinement) on the current layers, as
+ * gid_run does after each Gauss-Newton step: b = b_init + Delta b from the
+ * three K x K normal equations (FP64 Cholesky).  A singular block is reported
+ * as GID_ERR_NUMERIC by the next synchronising call.  Async. */
+int gid_base_color_step(gid_ctx* ctx);
+
 /* Exact energy of the current state (eq:giv-energy; the l1, l_p and max terms
  * exactly, not their IRLS surrogates): per_term[8] in the order data,
  * clustering, r-sparsity, r-consistency, monochrome, i-sparsity, smoothness,
@@ -297,13 +303,16 @@ int gid_net_adam_step(gid_net* net, float lr, float beta1, float beta2, float ep
 
 /* Learned initial state for the context's current frame: the network's r and
  * T (palette = the initial base colours) become the state, indirect values
- * T_1..T_K below the weights' eps written as exactly 0 (the i-sparsity prior's
- * default; the IRLS weights of Sec. 5.3 hold exact zeros, while a strictly
- * positive start has non-negativity weight 0 and overshoots), then, when base
+ * T_1..T_K below zero_below (>= 0) written as exactly 0 (the i-sparsity
+ * prior's default; the IRLS weights of Sec. 5.3 hold exact zeros, while a
+ * strictly positive value has non-negativity weight 0 and can overshoot
+ * below zero in the next Gauss-Newton step), T_0 refit per
+ * pixel to the data term (eq:data-term; closed form, clipped at 0) with R,
+ * T_1..T_K and b fixed, then, when base
  * colours are refined, one base-colour step (eq:basecolorrefinement) on those
  * layers.  Needs gid_set_base_colors and gid_set_frame, the same K, and H, W
  * multiples of 8.  Runs on the context stream.  Async. */
-int gid_init_learned(gid_ctx* ctx, gid_net* net);
+int gid_init_learned(gid_ctx* ctx, gid_net* net, float zero_below);
 
 /* ---- instrumentation ---- */
 

@@ -238,6 +238,21 @@ class Problem:
         return A, g
 
 
+def fit_direct(I, X, b):
+    """T_0 that minimises the data term (eq:data-term) at each pixel with r,
+    T_1..T_K and b fixed: the data residual is linear in T_0, so with
+    R = exp(r) and A_c = sum_k b_kc T_k the minimiser is
+    sum_c R_c (I_c - R_c A_c) / sum_c R_c^2, taken at 0 when negative (the
+    layers are non-negative, eq:nonnegativityterm).  Returns the new X."""
+    X = _f64(X).copy()
+    I = _f64(I)
+    b = _f64(b).reshape(-1, 3)
+    R = np.exp(X[:3])
+    A = np.einsum("kc,khw->chw", b, X[4:])
+    X[3] = np.maximum(np.sum(R * (I - R * A), axis=0) / np.sum(R * R, axis=0), 0.0)
+    return X
+
+
 def dense_solve(A, g):
     """Delta b (K, 3) from the three K x K blocks by SVD pseudo-inverse (Sec. 6.1)."""
     K = A.shape[1]

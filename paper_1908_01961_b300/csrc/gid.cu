@@ -44,6 +44,7 @@ struct gid_ctx {
   long long launches = 0;  // kernels launched by this context
   int apply_th = 4;        // rows per operator tile (gid_set_apply_tile / gid_autotune)
   int pcg_blocks = 0;      // > 0: run the PCG loop as one cooperative launch of this many blocks
+  int upd_cap = 148 * 4;   // vector-step blocks resident at once (SMs x blocks per SM)
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
   // CUDA graphs of gid_run's launch sequence, replayed on a context-owned stream
   struct Graph {
@@ -160,10 +161,12 @@ static dim3 pix_grid(const gid_ctx* c) { return dim3((c->W + BX - 1) / BX, (c->H
 static int dense_blocks(const gid_ctx* c) { return std::max(1, std::min(c->H, 296)); }
 // Blocks of the PCG operator step for the context's tile shape.
 static int apply_blocks(const gid_ctx* c) { return ((c->W + VTW - 1) / VTW) * ((c->H + c->apply_th - 1) / c->apply_th); }
-// Blocks of the PCG vector step: a few per SM, striding over the planes.
+// Blocks of the PCG vector step: exactly the blocks that are resident at once
+// (one wave), striding over the planes; a partial second wave would run a
+// quarter of the work on a fraction of the SMs.
 static int update_blocks(const gid_ctx* c) {
   const long items = (long)c->V * (c->plane / 4);
-  return (int)std::max(1L, std::min((items + 255) / 256, 148L * 4));
+  return (int)std::max(1L, std::min((items + 255) / 256, (long)c->upd_cap));
 }
 
 // ---------------------------------------------------------------- K dispatch
@@ -223,6 +226,16 @@ struct Launch {
       return 0;
     return coop ? sms * per_sm : 0;
   }
+  // Resident blocks of the vector step on this device (SMs x blocks per SM).
+  static int update_capacity(const gid_ctx*) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<K>, 256, 0) != cudaSuccess || per_sm < 1 ||
+        sms < 1)
+      return 148 * 4;
+    return std::min(sms * per_sm, 148 * 32);
+  }
   static void update(const gid_ctx* c, int it, const float* p, int last) {
     k_update<K><<<update_blocks(c), 256, 0, c->stream>>>(params(c), it, apply_blocks(c), p, last);
   }
@@ -231,6 +244,7 @@ struct Launch {
   }
   static void energy(const gid_ctx* c) { k_energy<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void init_cold(const gid_ctx* c) { k_init_cold<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
+  static void fit_direct(const gid_ctx* c) { k_fit_direct<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void readout(const gid_ctx* c, float* R, float* T) {
     k_readout<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), R, T);
   }
@@ -343,6 +357,19 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
   const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
   const size_t pbytes = (size_t)npart * sizeof(double);
+  switch (c->K) {
+    case 1: c->upd_cap = Launch<1>::update_capacity(c); break;
+    case 2: c->upd_cap = Launch<2>::update_capacity(c); break;
+    case 3: c->upd_cap = Launch<3>::update_capacity(c); break;
+    case 4: c->upd_cap = Launch<4>::update_capacity(c); break;
+    case 5: c->upd_cap = Launch<5>::update_capacity(c); break;
+    case 6: c->upd_cap = Launch<6>::update_capacity(c); break;
+    case 7: c->upd_cap = Launch<7>::update_capacity(c); break;
+    case 8: c->upd_cap = Launch<8>::update_capacity(c); break;
+    case 9: c->upd_cap = Launch<9>::update_capacity(c); break;
+    default: c->upd_cap = Launch<10>::update_capacity(c); break;
+  }
+  cudaGetLastError();
   c->nbmax = (int)std::max({(long)update_blocks(c), (long)((W + VTW - 1) / VTW) * ((H + 1) / 2), 148L * 32});
   const size_t ppbytes = sizeof(double) * 4 * (size_t)c->nbmax;
   c->pool_bytes = fbytes + lbytes + 256 * 9 + sizeof(DevColors) + sizeof(DevScalars) + pbytes + ppbytes;
@@ -509,8 +536,16 @@ extern "C" int gid_init(gid_ctx* c, int mode) {
   return GID_OK;
 }
 
-extern "C" int gid_init_learned(gid_ctx* c, gid_net* net) {
+extern "C" int gid_base_color_step(gid_ctx* c) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (!c->has_frame || !c->initialised || !c->has_colors) return fail(c, GID_ERR_STATE, "no frame/state/colours");
+  launch(c, GID_KIND_DENSE, [&] { GID_DISPATCH(c, dense, c, 1); });
+  return check_launch(c, "k_dense");
+}
+
+extern "C" int gid_init_learned(gid_ctx* c, gid_net* net, float zero_below) {
   if (!c || !net) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (!(zero_below >= 0.f) || !std::isfinite(zero_below)) return fail(c, GID_ERR_INVALID_ARG, "zero_below >= 0");
   if (!c->has_frame || !c->has_colors)
     return fail(c, GID_ERR_STATE, "gid_init_learned needs gid_set_base_colors and gid_set_frame");
   if (gidnet_K(net) != c->K) return fail(c, GID_ERR_INVALID_ARG, "network and context have different K");
@@ -519,13 +554,15 @@ extern "C" int gid_init_learned(gid_ctx* c, gid_net* net) {
   const float* palette = reinterpret_cast<const float*>(reinterpret_cast<const char*>(c->col) +
                                                         offsetof(DevColors, binit));
   std::string msg;
-  // Indirect values below the IRLS epsilon start at exactly zero: the sparse
-  // prior's default state, which the reweighting of Sec. 5.3 keeps from
-  // overshooting below zero (a strictly positive start has non-negativity
-  // weight zero everywhere).
-  if (int rc = gidnet_infer_planes(net, c->H, c->W, c->I, c->plane, c->pitch, c->lab, palette, c->w.eps, c->X,
+  // Indirect values below zero_below start at exactly zero: the sparse prior's
+  // default state, which the reweighting of Sec. 5.3 keeps from overshooting
+  // below zero (a strictly positive value has non-negativity weight zero).
+  if (int rc = gidnet_infer_planes(net, c->H, c->W, c->I, c->plane, c->pitch, c->lab, palette, zero_below, c->X,
                                    c->stream, &c->launches, &msg))
     return fail(c, rc, "network forward", msg.c_str());
+  // T_0 refit to the data term per pixel (closed form) on the predicted R and T_1..T_K
+  launch(c, GID_KIND_INIT, [&] { GID_DISPATCH(c, fit_direct, c); });
+  if (int rc = check_launch(c, "k_fit_direct")) return rc;
   if (c->w.refine_base_colors != 0) {
     launch(c, GID_KIND_DENSE, [&] { GID_DISPATCH(c, dense, c, 1); });
     if (int rc = check_launch(c, "k_dense")) return rc;

@@ -422,6 +422,29 @@ __global__ void k_init_cold(Params P) {
   for (int k = 1; k <= K; k++) P.X[(3 + k) * P.plane + o] = 0.f;
 }
 
+// T_0 minimising the data term (eq:data-term) per pixel with r, T_1..T_K and
+// the current b fixed: sum_c R_c (I_c - R_c A_c) / sum_c R_c^2 with
+// A_c = sum_k b_kc T_k, taken at 0 when negative.
+template <int K>
+__global__ void k_fit_direct(Params P) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  const long o = off2(P, y, x);
+  float T[K + 1];
+#pragma unroll
+  for (int k = 1; k <= K; k++) T[k] = P.X[(3 + k) * P.plane + o];
+  float num = 0.f, den = 0.f;
+  for (int c = 0; c < 3; c++) {
+    const float R = expf(P.X[c * P.plane + o]);
+    float A = 0.f;
+#pragma unroll
+    for (int k = 1; k <= K; k++) A += P.col->b[(k - 1) * 3 + c] * T[k];
+    num += R * (P.I[c * P.plane + o] - R * A);
+    den += R * R;
+  }
+  P.X[3 * P.plane + o] = fmaxf(num / den, 0.f);
+}
+
 // Shared per-pixel state at the linearisation point.
 template <int K>
 struct PixState {
@@ -676,6 +699,12 @@ struct ApplyShape<17> {
 // p = s (+ beta p_old) on the tile's pixels.  get_beta() is called once the
 // staging loads are in (it may wait on a block reduction).  Returns this
 // thread's share of <p, q>.  All threads of the block call it.
+// Bulk prefetch of bytes [p, p + bytes) into L2 (no registers, no completion
+// to wait for); p 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int K, int TH, class GB>
 __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t, const ColorTable<K>& ct, int x0, int y0,
                                             int mode, int first, GB get_beta, const float* pin, float* pout,
@@ -684,11 +713,26 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
   constexpr int NCH = VRW / 4;  // float4 chunks per staged row
   constexpr int NTH = BX * TH;  // threads per block
   const int tid = tid_flat();
+  // The compute phase reads every coefficient plane (and p_old, q_old) at the
+  // tile's own pixels: start all of those rows towards L2 now, so that their
+  // DRAM latency overlaps the staging below instead of the dependent math.
+  {
+    constexpr int V = K + 4;
+    const int nc = coef_planes(K, P.ns), npl = nc + ((mode == 0 && !first) ? 2 * V : 0);
+    const unsigned bytes = 4u * (unsigned)min(VTW, P.pitch - x0);
+    for (int i = tid; i < npl * TH; i += NTH) {
+      const int pl = i / TH, y = y0 + (i - pl * TH);
+      if (y >= P.H) continue;
+      const float* base = pl < nc ? P.coef + (long)pl * P.plane
+                                  : (pl < nc + V ? pin + (long)(pl - nc) * P.plane : qout + (long)(pl - nc - V) * P.plane);
+      prefetch_l2(base + off2(P, y, x0), bytes);
+    }
+  }
   // Stage s = z (PCG step) or s = pin (stage call) with its halo.  Each thread
   // issues up to SB chunk loads before storing any, so a block needs only a
   // couple of memory round trips.
   const float* __restrict__ sv = mode == 0 ? P.z : pin;
-  constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH, SB = 8;
+  constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH, SB = TH >= 17 ? 4 : 8;
   auto chunk_dst = [&](int i, int& gy, int& gx, int& v) -> float* {
     if (i < NR) {
       const int c = i / ((TH + 2 * AHR) * NCH), rem = i - c * (TH + 2 * AHR) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
@@ -750,64 +794,67 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
       pq += dot4(p, q);
     };
     const int cx = VHX + QW * threadIdx.x, ry = threadIdx.y + AHR, ty = threadIdx.y + 1;
-    // data and monochrome blocks: P_c = sum_k b_kc p_Tk, M_c = sum_k dm_kc p_Tk
-    F4 Pc[3], Mc[3];
+    // data block: P_c = sum_k b_kc p_Tk
+    F4 u[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) Pc[c] = Mc[c] = f4s(0.f);
+    for (int c = 0; c < 3; c++) u[c] = f4s(0.f);
 #pragma unroll
     for (int k = 0; k <= K; k++) {
       const F4 pk = lds4(&t.pt[k][ty][cx]);
 #pragma unroll
-      for (int c = 0; c < 3; c++) {
-        Pc[c] = fma4(f4s(ct.b[k][c]), pk, Pc[c]);
-        Mc[c] = fma4(f4s(ct.dm[k][c]), pk, Mc[c]);
-      }
+      for (int c = 0; c < 3; c++) u[c] = fma4(f4s(ct.b[k][c]), pk, u[c]);
     }
-    const F4 wm = ldg4(cf + CL::WM * PL), dr = ldg4(cf + CL::DR * PL);
-    F4 u[3];
-    // reflectance channels: data, clustering/temporal diagonal, r-sparsity, consistency
-    const F4 eR = ldg4(cf + CL::WR * PL), eD = ldg4(cf + CL::WD * PL);
+    // reflectance channels, one at a time: data, clustering/temporal diagonal,
+    // r-sparsity, consistency pairs (x, x + o_j) and (x - o_j, x); the shared
+    // per-pixel weights are re-read through L1 rather than held in registers
     const float eLm = hL ? cf[CL::WR * PL - 1] : 0.f;
-    const F4 eL = f4v(eLm, eR.a.x, eR.a.y, eR.b.x);
-    const F4 eU = hU ? ldg4(cf + CL::WD * PL - P.pitch) : f4s(0.f);
-    F4 qr[3], pcr[3];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       const F4 Sc = ldg4(cf + (CL::S + c) * PL), Ac = ldg4(cf + (CL::A + c) * PL);
       const float* row = &t.pr[c][ry][cx];
       const F4 pc = lds4(row);
-      pcr[c] = pc;
-      u[c] = mul4(Ac, fma4(Sc, pc, Pc[c]));
-      const F4 right = f4v(pc.a.y, pc.b.x, pc.b.y, row[4]);
-      const F4 left = f4v(row[-1], pc.a.x, pc.a.y, pc.b.x);
-      const F4 down = lds4(&t.pr[c][ry + 1][cx]), up = lds4(&t.pr[c][ry - 1][cx]);
-      F4 q = fma4(Sc, u[c], mul4(dr, pc));
-      q = fma4(eR, sub4(pc, right), q);
-      q = fma4(eL, sub4(pc, left), q);
-      q = fma4(eD, sub4(pc, down), q);
-      qr[c] = fma4(eU, sub4(pc, up), q);
-    }
-    // consistency pairs (x, x + o_j) and (x - o_j, x): weights from the coefficient planes
+      u[c] = mul4(Ac, fma4(Sc, pc, u[c]));  // u_c = A_c (S_c p_rc + P_c)
+      F4 q = fma4(Sc, u[c], mul4(ldg4(cf + CL::DR * PL), pc));
+      {
+        const F4 eR = ldg4(cf + CL::WR * PL), eD = ldg4(cf + CL::WD * PL);
+        const F4 eL = f4v(eLm, eR.a.x, eR.a.y, eR.b.x);
+        const F4 right = f4v(pc.a.y, pc.b.x, pc.b.y, row[4]);
+        const F4 left = f4v(row[-1], pc.a.x, pc.a.y, pc.b.x);
+        q = fma4(eR, sub4(pc, right), q);
+        q = fma4(eL, sub4(pc, left), q);
+        q = fma4(eD, sub4(pc, lds4(&t.pr[c][ry + 1][cx])), q);
+        if (hU) q = fma4(ldg4(cf + CL::WD * PL - P.pitch), sub4(pc, lds4(&t.pr[c][ry - 1][cx])), q);
+      }
 #pragma unroll
-    for (int j = 0; j < GID_MAX_PAIRS; j++) {
-      if (j < P.ns) {
-        const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
-        const F4 of = ldg4(cf + (CL::CW + j) * PL), ob = ldg4(cf + (CL::CW + P.ns + j) * PL);
-#pragma unroll
-        for (int c = 0; c < 3; c++) {
+      for (int j = 0; j < GID_MAX_PAIRS; j++) {
+        if (j < P.ns) {
+          const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
           const float* fw = &t.pr[c][ry + dy][cx + dx];
           const float* bw = &t.pr[c][ry - dy][cx - dx];
-          qr[c] = fma4(of, sub4(pcr[c], f4v(fw[0], fw[1], fw[2], fw[3])), qr[c]);
-          qr[c] = fma4(ob, sub4(pcr[c], f4v(bw[0], bw[1], bw[2], bw[3])), qr[c]);
+          q = fma4(ldg4(cf + (CL::CW + j) * PL), sub4(pc, f4v(fw[0], fw[1], fw[2], fw[3])), q);
+          q = fma4(ldg4(cf + (CL::CW + P.ns + j) * PL), sub4(pc, f4v(bw[0], bw[1], bw[2], bw[3])), q);
         }
       }
+      finish(c, pc, q);
     }
+    // monochrome block: M_c = w_m sum_k dm_kc p_Tk
+    F4 Mc[3];
 #pragma unroll
-    for (int c = 0; c < 3; c++) finish(c, pcr[c], qr[c]);
+    for (int c = 0; c < 3; c++) Mc[c] = f4s(0.f);
 #pragma unroll
-    for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
+    for (int k = 0; k <= K; k++) {
+      const F4 pk = lds4(&t.pt[k][ty][cx]);
+#pragma unroll
+      for (int c = 0; c < 3; c++) Mc[c] = fma4(f4s(ct.dm[k][c]), pk, Mc[c]);
+    }
+    {
+      const F4 wm = ldg4(cf + CL::WM * PL);
+#pragma unroll
+      for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
+    }
     // layers: data and monochrome back-projections, diagonal IRLS weights, smoothness
-#pragma unroll
+    // (not unrolled for the one-wave tile: its register budget is 96 per thread)
+#pragma unroll(TH >= 17 ? 1 : K + 1)
     for (int k = 0; k <= K; k++) {
       const float* row = &t.pt[k][ty][cx];
       const F4 pk = lds4(row);
@@ -939,7 +986,7 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
 // zero).  A grid of a few blocks per SM strides over all V x plane / 4 float4
 // items.
 template <int K>
-__global__ void __launch_bounds__(256) k_update(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
+__global__ void __launch_bounds__(256, 4) k_update(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
   // alpha = rho_it / <p, q>_it from the operator step's partials
   const double pq = block_total(part_share(pcg_partials(P, PART_PQ, it), nb_prev));
   const float alpha = pq != 0.0 ? (float)(P.sc->rho2[it & 1] / pq) : 0.f;

@@ -34,7 +34,7 @@ EXPORTS = (
     "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
     "gid_net_set_weights", "gid_net_get_weights", "gid_net_get_grads", "gid_net_forward", "gid_net_backward",
-    "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned",
+    "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned", "gid_base_color_step",
 )
 
 
@@ -129,7 +129,8 @@ def load():
     L.gid_net_backward.argtypes = [P, I, I, I, P, P, P, P, P, D]
     L.gid_net_adam_step.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     L.gid_net_set_loss_weights.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float]
-    L.gid_init_learned.argtypes = [P, P]
+    L.gid_init_learned.argtypes = [P, P, ctypes.c_float]
+    L.gid_base_color_step.argtypes = [P]
     for n in EXPORTS:
         if n not in ("gid_default_weights", "gid_destroy", "gid_last_error", "gid_batch_destroy",
                      "gid_batch_last_error", "gid_batch_ctx", "gid_net_destroy", "gid_net_last_error",
@@ -245,9 +246,9 @@ class Solver:
     def init(self, mode: int = 0):
         self._chk(self.lib.gid_init(self.h, mode))
 
-    def init_learned(self, net: "Net"):
+    def init_learned(self, net: "Net", zero_below: float = 0.0):
         """Initial state from the warm-start network (gid_init_learned)."""
-        self._chk(self.lib.gid_init_learned(self.h, net.h))
+        self._chk(self.lib.gid_init_learned(self.h, net.h, zero_below))
 
     def run(self, n_outer: int, m_inner: int):
         self._chk(self.lib.gid_run(self.h, n_outer, m_inner))
@@ -269,6 +270,10 @@ class Solver:
     def set_state(self, X):
         self._check_dev(X, (self.V, self.H, self.W), self.torch.float32)
         self._chk(self.lib.gid_set_state(self.h, _ptr(X)))
+
+    def base_color_step(self):
+        """One base-colour step on the current layers (gid_base_color_step)."""
+        self._chk(self.lib.gid_base_color_step(self.h))
 
     def energy(self):
         tot = ctypes.c_double()

@@ -17,7 +17,8 @@ which its exact energy is at or below the cold start's final energy.
 
 Command line:
     python -m paper_1908_01961_b300.warmstart train --frames 1000 --steps 6000 --out FILE.npy
-    python -m paper_1908_01961_b300.warmstart evaluate --weights FILE.npy --frames 20
+    python -m paper_1908_01961_b300.warmstart evaluate --weights FILE.npy --eval-frames 20
+    python -m paper_1908_01961_b300.warmstart sensitivity --eval-frames 4
 """
 from __future__ import annotations
 
@@ -40,6 +41,11 @@ WIDTHS = (32, 64, 96, 128)
 # factor their error hardly registers in the loss and the network predicts
 # them as zero, a state the IRLS weights of Sec. 5.3 leave only slowly.
 LOSS_WEIGHTS = (1.0, 1.0, 10.0)
+# Predicted indirect values below this start at exactly zero (gid_init_learned).
+# Swept over 0.002 .. 0.04 on held-out frames: below ~0.005 the first
+# Gauss-Newton step overshoots small positive values below zero (non-negativity
+# weight 0 for T > 0); above ~0.01 the start's indirect layers are mostly zero.
+ZERO_BELOW = 0.01
 HERE = os.path.dirname(os.path.abspath(__file__))
 DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart_K6.npy")
 
@@ -52,17 +58,17 @@ def solver_weights():
 
 
 def _make_frame(args):
-    seed, t = args
-    v = synth.SyntheticVideo(H, W, K, N_CELLS, seed=seed, noise=NOISE)
-    f = v.frame(t)
+    seed, t, noise = args
+    v = synth.SyntheticVideo(H, W, K, N_CELLS, seed=seed, noise=noise)
+    f = v.frame(t, noise=noise > 0)
     b = synth.initial_base_colors(f.I, f.labels, K)
     return f.I.astype(np.float32), f.labels.astype(np.uint8), b.astype(np.float32)
 
 
-def generate(seeds, workers=None):
+def generate(seeds, workers=None, noise=NOISE):
     """Frames (I, labels, b_init) for the given seeds; frame t = seed mod 30 of
     each seed's video (so the light direction varies as in the video)."""
-    jobs = [(int(s), int(s) % 30) for s in seeds]
+    jobs = [(int(s), int(s) % 30, float(noise)) for s in seeds]
     workers = workers or max(1, min(32, (os.cpu_count() or 2) - 1, len(jobs)))
     if workers == 1:
         return [_make_frame(j) for j in jobs]
@@ -147,10 +153,13 @@ def energies(solver, n_outer=N_OUTER, m_inner=M_INNER):
     return np.array(tot), np.array(per)
 
 
-def evaluate(net, frames, n_outer=N_OUTER, m_inner=M_INNER, log=None):
-    """Per frame: energies of the cold and the learned start after 0..n_outer
-    Gauss-Newton steps, and the learned start's step count to reach the cold
-    start's final energy (n_outer + 1 if it never does)."""
+def evaluate(net, frames, n_outer=N_OUTER, m_inner=M_INNER, zero_below=(None,), log=None, learned_steps=None):
+    """Per frame: energies of the cold start after 0..n_outer Gauss-Newton
+    steps and of the learned start after 0..learned_steps (default n_outer),
+    and the learned start's step count to reach the cold start's final energy
+    (learned_steps + 1 if it never does), for each threshold in zero_below
+    (None = ZERO_BELOW)."""
+    learned_steps = n_outer if learned_steps is None else learned_steps
     import torch
     s = gid.Solver(H, W, K, solver_weights())
     out = []
@@ -160,15 +169,54 @@ def evaluate(net, frames, n_outer=N_OUTER, m_inner=M_INNER, log=None):
         s.set_frame(rgb, lb)
         s.init(0)
         Ec, Pc = energies(s, n_outer, m_inner)
+        rec = dict(E_cold=Ec.tolist(), terms_cold=Pc.tolist(), learned={})
+        for zb in zero_below:
+            zb = ZERO_BELOW if zb is None else zb
+            s.set_base_colors(b)
+            s.init_learned(net, zb)
+            El, Pl = energies(s, learned_steps, m_inner)
+            hit = np.nonzero(El <= Ec[-1])[0]
+            n_l = int(hit[0]) if len(hit) else learned_steps + 1
+            rec["learned"][str(zb)] = dict(E=El.tolist(), terms=Pl.tolist(), n=n_l)
+            if log:
+                log(f"frame {i} zero_below {zb}: cold E {Ec[0]:.4e} -> {Ec[-1]:.4e}; learned E0 {El[0]:.4e}, "
+                    f"reaches it after {n_l} steps")
+        out.append(rec)
+    s.close()
+    return out
+
+
+def sensitivity(frames, amplitudes=(0.001, 0.003, 0.01), seed=0, n_outer=N_OUTER, m_inner=M_INNER, log=None):
+    """How accurate a start must be to save Gauss-Newton steps: per frame, the
+    plain solve's result X* (cold start, n_outer steps) plus Gaussian noise of
+    each amplitude (indirect values then clipped at 0), one base-colour step,
+    then the steps needed to return to the plain solve's final energy
+    (n_outer + 1 if not within n_outer)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    s = gid.Solver(H, W, K, solver_weights())
+    out = []
+    for i, (I, lab, b) in enumerate(frames):
+        rgb, lb = torch.from_numpy(I).cuda(), torch.from_numpy(lab).cuda()
         s.set_base_colors(b)
-        s.init_learned(net)
-        El, Pl = energies(s, n_outer, m_inner)
-        hit = np.nonzero(El <= Ec[-1])[0]
-        n_l = int(hit[0]) if len(hit) else n_outer + 1
-        out.append(dict(E_cold=Ec.tolist(), E_learned=El.tolist(), n_learned=n_l,
-                        terms_cold=Pc.tolist(), terms_learned=Pl.tolist()))
+        s.set_frame(rgb, lb)
+        s.init(0)
+        s.run(n_outer, m_inner)
+        E_star, _ = s.energy()
+        Xs = s.state().cpu().numpy()
+        rec = dict(E_star=E_star, steps={})
+        for a in (0.0,) + tuple(amplitudes):
+            X0 = Xs + rng.normal(0.0, a, Xs.shape) if a else Xs.copy()
+            X0[4:] = np.maximum(X0[4:], 0.0)
+            s.set_base_colors(b)
+            s.set_state(torch.from_numpy(np.ascontiguousarray(X0, np.float32)).cuda())
+            s.base_color_step()
+            E, _ = energies(s, n_outer, m_inner)
+            hit = np.nonzero(E <= E_star)[0]
+            rec["steps"][str(a)] = int(hit[0]) if len(hit) else n_outer + 1
+        out.append(rec)
         if log:
-            log(f"frame {i}: cold E {Ec[0]:.4e} -> {Ec[-1]:.4e}; learned E0 {El[0]:.4e}, reaches it after {n_l} steps")
+            log(f"frame {i}: steps back to the plain solve's energy by start noise RMS: {rec['steps']}")
     s.close()
     return out
 
@@ -181,7 +229,7 @@ def load_net(path=DEFAULT_WEIGHTS, stream=None):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("cmd", choices=("train", "evaluate"))
+    ap.add_argument("cmd", choices=("train", "evaluate", "sensitivity"))
     ap.add_argument("--frames", type=int, default=1000)
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=8)
@@ -191,6 +239,9 @@ def main(argv=None):
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--weights", default=DEFAULT_WEIGHTS)
     ap.add_argument("--eval-frames", type=int, default=10)
+    ap.add_argument("--eval-noise", type=float, default=NOISE, help="noise sigma of the evaluation frames")
+    ap.add_argument("--zero-below", type=float, nargs="*", default=None,
+                    help="thresholds of the learned start to evaluate (default: ZERO_BELOW)")
     ap.add_argument("--report", default=None, help="write a JSON summary here")
     a = ap.parse_args(argv)
 
@@ -198,6 +249,13 @@ def main(argv=None):
         print(m, flush=True)
 
     report = {}
+    if a.cmd == "sensitivity":
+        sens = sensitivity(generate(range(EVAL_SEED0, EVAL_SEED0 + a.eval_frames)), log=log)
+        report.update(eval_frames=a.eval_frames, sensitivity=sens)
+        if a.report:
+            with open(a.report, "w") as f:
+                json.dump(report, f, indent=1)
+        return
     if a.cmd == "train":
         t0 = time.time()
         frames = generate(range(TRAIN_SEED0, TRAIN_SEED0 + a.frames))
@@ -220,11 +278,16 @@ def main(argv=None):
     else:
         net = load_net(a.weights)
     if a.eval_frames > 0:
-        ev = evaluate(net, generate(range(EVAL_SEED0, EVAL_SEED0 + a.eval_frames)), log=log)
-        n = [e["n_learned"] for e in ev]
-        report.update(eval_frames=a.eval_frames, n_learned=n, n_learned_max=max(n), n_cold=N_OUTER,
-                      mean_ratio=float(np.mean(n)) / N_OUTER, frames=ev)
-        log(f"learned start reaches the cold-start energy after {n} Gauss-Newton steps (cold: {N_OUTER})")
+        zbs = a.zero_below or [ZERO_BELOW]
+        ev = evaluate(net, generate(range(EVAL_SEED0, EVAL_SEED0 + a.eval_frames), noise=a.eval_noise),
+                      zero_below=zbs, log=log)
+        summary = {}
+        for zb in zbs:
+            n = [e["learned"][str(zb)]["n"] for e in ev]
+            summary[str(zb)] = dict(n_learned=n, n_learned_max=max(n), mean_ratio=float(np.mean(n)) / N_OUTER)
+            log(f"zero_below {zb}: learned start reaches the cold-start energy after {n} Gauss-Newton steps "
+                f"(cold: {N_OUTER})")
+        report.update(eval_frames=a.eval_frames, eval_noise=a.eval_noise, n_cold=N_OUTER, summary=summary, frames=ev)
     if a.report:
         with open(a.report, "w") as f:
             json.dump(report, f, indent=1)

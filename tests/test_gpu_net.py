@@ -149,7 +149,7 @@ def test_invalid_arguments():
 def test_learned_init_is_the_network_output_then_one_base_colour_step():
     """gid_init_learned: state = the network's (r, T) on the frame with palette =
     the initial base colours (bit-equal to gid_net_forward, indirect values below
-    eps set to 0), then b = b_init +
+    zero_below set to 0), T_0 refit to the data term (oracle: fit_direct), then b = b_init +
     Delta b from the base-colour step on those layers (oracle: SVD solve)."""
     import oracle as O
     from harness import Case
@@ -159,18 +159,24 @@ def test_learned_init_is_the_network_output_then_one_base_colour_step():
     rgb, lab = case.gpu_inputs()
     s.set_frame(rgb, lab)
     net = gid.Net(case.K, seed=3)
-    s.init_learned(net)
+    zb = 0.004
+    s.init_learned(net, zb)
     X = s.state()
     pal = torch.from_numpy(case.b_init.astype(np.float32)).cuda()[None].contiguous()
     r, T = net.forward(rgb[None].contiguous(), lab[None].contiguous(), pal)
     torch.cuda.synchronize()
     X = X.cpu().numpy()
     T = T[0].cpu().numpy()
-    T[1:][T[1:] < s.weights.eps] = 0.0                    # indirect values below eps start at zero
-    assert np.array_equal(X[:3], r[0].cpu().numpy()) and np.array_equal(X[3:], T)
+    T[1:][T[1:] < zb] = 0.0                               # indirect values below zero_below start at zero
+    assert np.array_equal(X[:3], r[0].cpu().numpy()) and np.array_equal(X[4:], T[1:])
+    Xn = np.concatenate([r[0].cpu().numpy(), T]).astype(np.float64)
+    T0 = O.fit_direct(case.frames[0].I.astype(np.float32), Xn, case.b_init)[3]
+    assert np.abs(X[3] - T0).max() <= 1e-5 * max(1.0, np.abs(T0).max())
     pb = case.oracle_problem()
     A, g = pb.dense_normal(X.astype(np.float64))
     b_ref = case.b_init + O.dense_solve(A, g)
     assert np.abs(s.base_colors() - b_ref).max() <= 1e-3
     with pytest.raises(gid.GidError):
         s.init_learned(gid.Net(3))                       # K mismatch
+    with pytest.raises(gid.GidError):
+        s.init_learned(net, -1.0)

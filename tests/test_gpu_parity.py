@@ -258,3 +258,19 @@ def test_persistent_pcg_matches_oracle(name):
     assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
     assert np.abs(s.base_colors() - bo).max() <= 1e-3
     assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+def test_base_color_step_matches_oracle():
+    """gid_base_color_step on a set state: b = b_init + Delta b of the oracle's
+    SVD solve of the same normal equations."""
+    case = Case(**CASES["64x48_K4"], seed=7)
+    s = case.solver()
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    pb = case.oracle_problem()
+    X = random_state(case, pb, 8)
+    X[4:] = np.abs(X[4:])
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    s.base_color_step()
+    A, g = pb.dense_normal(X)
+    assert np.abs(s.base_colors() - (case.b_init + O.dense_solve(A, g))).max() <= 1e-4

@@ -173,3 +173,27 @@ def test_temporal_pairs_weight_and_energy():
     e1 = sum(10 * om_t[1][y, x] * np.sum((X[:3, y, x] - rprev[:, y + 1, x + 1]) ** 2)
              for y in range(H - 1) for x in range(W - 1))
     assert E == pytest.approx(10 * 3 * 0.01 * H * W + e1, rel=1e-12)
+
+
+def test_fit_direct_recovers_ground_truth_and_minimises_the_data_term():
+    """At a noise-free frame the per-pixel refit of T_0 returns the true T_0
+    (zero data residual); on a noisy frame it is the minimiser of the data term
+    over T_0 (every perturbation raises it) and it is clipped at zero."""
+    v = synth.SyntheticVideo(24, 32, 4, 6, seed=5, noise=0.0)
+    f = v.frame(0, noise=False)
+    X = np.concatenate([np.log(f.R), f.T])
+    Xw = X.copy()
+    Xw[3] = 0.3                                             # a wrong T_0
+    assert np.allclose(O.fit_direct(f.I, Xw, f.b)[3], f.T[0], rtol=1e-12, atol=1e-14)
+    rng = np.random.default_rng(2)
+    I = f.I + rng.normal(0, 0.02, f.I.shape)
+    pb = make_problem(24, 32, 4, I=I, labels=f.labels, b=f.b)
+    Xf = O.fit_direct(I, Xw, f.b)
+    E0 = pb.energy(Xf)[0]
+    for d in (1e-3, -1e-3):
+        Xp = Xf.copy()
+        Xp[3] += d
+        assert pb.energy(Xp)[0] > E0
+    Xn = Xw.copy()
+    Xn[4:] = 5.0                                            # indirect light far above the image
+    assert np.all(O.fit_direct(f.I, Xn, f.b)[3] == 0.0)
