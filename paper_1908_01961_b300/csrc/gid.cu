@@ -176,12 +176,30 @@ struct Launch {
   static void linearize(const gid_ctx* c, int mode, float* g, float* dg) {
     k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg);
   }
+  // k_apply and k_update are launched as programmatic dependents of the kernel
+  // before them: each may start (prefetch, colour table) while that kernel
+  // drains, and waits on it in-kernel (griddepcontrol.wait) before reading
+  // anything it wrote.  After any other kernel the launch is ordered as usual.
+  template <class... KA, class... A>
+  static void launch_pdl(const gid_ctx* c, void (*kern)(KA...), dim3 grid, dim3 block, size_t smem, A... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, kern, args...);
+  }
   template <int TH>
   static void apply_th(const gid_ctx* c, int mode, int first, int it, const float* pin, float* pout, float* qout) {
     const size_t smem = sizeof(ApplyTile<K, TH>);
     const dim3 grid((c->W + VTW - 1) / VTW, (c->H + TH - 1) / TH);
-    k_apply<K, TH><<<grid, dim3(BX, TH), smem, c->stream>>>(params(c), mode, first, it, update_blocks(c), pin, pout,
-                                                             qout);
+    launch_pdl(c, k_apply<K, TH>, grid, dim3(BX, TH), smem, params(c), mode, first, it, update_blocks(c), pin, pout,
+               qout);
   }
   // Opt every operator tile shape in to its dynamic shared memory (before any graph capture).
   static void prepare(const gid_ctx*) {
@@ -237,7 +255,7 @@ struct Launch {
     return std::min(sms * per_sm, 148 * 32);
   }
   static void update(const gid_ctx* c, int it, const float* p, int last) {
-    k_update<K><<<update_blocks(c), 256, 0, c->stream>>>(params(c), it, apply_blocks(c), p, last);
+    launch_pdl(c, k_update<K>, dim3(update_blocks(c)), dim3(256), 0, params(c), it, apply_blocks(c), p, last);
   }
   static void dense(const gid_ctx* c, int solve) {
     k_dense<K><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);

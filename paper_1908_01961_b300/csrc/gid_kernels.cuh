@@ -705,6 +705,32 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// The operator tile's compute phase reads every coefficient plane (and p_old,
+// q_old) at the tile's own pixels: start all of those rows towards L2, so that
+// their DRAM latency overlaps the staging instead of the dependent math.  None
+// of them is written by the PCG vector step, so this may run before the grid
+// dependency on it is resolved.
+template <int K, int TH>
+__device__ __forceinline__ void prefetch_tile(const Params& P, int x0, int y0, int mode, int first, const float* pin,
+                                              const float* qout) {
+  constexpr int V = K + 4, NTH = BX * TH;
+  const int nc = coef_planes(K, P.ns), npl = nc + ((mode == 0 && !first) ? 2 * V : 0);
+  const unsigned bytes = 4u * (unsigned)min(VTW, P.pitch - x0);
+  for (int i = tid_flat(); i < npl * TH; i += NTH) {
+    const int pl = i / TH, y = y0 + (i - pl * TH);
+    if (y >= P.H) continue;
+    const float* base = pl < nc ? P.coef + (long)pl * P.plane
+                                : (pl < nc + V ? pin + (long)(pl - nc) * P.plane : qout + (long)(pl - nc - V) * P.plane);
+    prefetch_l2(base + off2(P, y, x0), bytes);
+  }
+}
+
+// Programmatic dependent launch: wait until the grid this one depends on has
+// completed and its writes are visible (a no-op for an ordinary launch), and
+// let the next grid in the stream begin launching.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
+
 template <int K, int TH, class GB>
 __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t, const ColorTable<K>& ct, int x0, int y0,
                                             int mode, int first, GB get_beta, const float* pin, float* pout,
@@ -713,21 +739,6 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
   constexpr int NCH = VRW / 4;  // float4 chunks per staged row
   constexpr int NTH = BX * TH;  // threads per block
   const int tid = tid_flat();
-  // The compute phase reads every coefficient plane (and p_old, q_old) at the
-  // tile's own pixels: start all of those rows towards L2 now, so that their
-  // DRAM latency overlaps the staging below instead of the dependent math.
-  {
-    constexpr int V = K + 4;
-    const int nc = coef_planes(K, P.ns), npl = nc + ((mode == 0 && !first) ? 2 * V : 0);
-    const unsigned bytes = 4u * (unsigned)min(VTW, P.pitch - x0);
-    for (int i = tid; i < npl * TH; i += NTH) {
-      const int pl = i / TH, y = y0 + (i - pl * TH);
-      if (y >= P.H) continue;
-      const float* base = pl < nc ? P.coef + (long)pl * P.plane
-                                  : (pl < nc + V ? pin + (long)(pl - nc) * P.plane : qout + (long)(pl - nc - V) * P.plane);
-      prefetch_l2(base + off2(P, y, x0), bytes);
-    }
-  }
   // Stage s = z (PCG step) or s = pin (stage call) with its halo.  Each thread
   // issues up to SB chunk loads before storing any, so a block needs only a
   // couple of memory round trips.
@@ -889,6 +900,10 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
   ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
+  prefetch_tile<K, TH>(P, blockIdx.x * VTW, blockIdx.y * TH, mode, first, pin, qout);
+  // everything below reads what the previous PCG vector step wrote
+  grid_dep_wait();
+  grid_dep_release();
   const bool use_beta = mode == 0 && !first;
   // this thread's share of rho_it = <r, z> from the previous vector step's partials
   const double rho_share = use_beta ? part_share(pcg_partials(P, PART_RZ, it - 1), nb_prev) : 0.0;
@@ -987,6 +1002,8 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
 // items.
 template <int K>
 __global__ void __launch_bounds__(256, 4) k_update(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
+  grid_dep_wait();  // the operator step's p, q and partials
+  grid_dep_release();
   // alpha = rho_it / <p, q>_it from the operator step's partials
   const double pq = block_total(part_share(pcg_partials(P, PART_PQ, it), nb_prev));
   const float alpha = pq != 0.0 ? (float)(P.sc->rho2[it & 1] / pq) : 0.f;
@@ -1057,6 +1074,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     const float beta = first ? 0.f : (rho_old != 0.0 ? (float)(rho / rho_old) : 0.f);
     float pq = 0.f;
     for (int tile = b; tile < ntiles; tile += nb) {
+      prefetch_tile<K, TH>(P, (tile % ntx) * VTW, (tile / ntx) * TH, 0, first, p, q);
       pq += apply_tile<K, TH>(P, t, ct, (tile % ntx) * VTW, (tile / ntx) * TH, 0, first, [&]() { return beta; }, p, p,
                               q);
       __syncthreads();  // the next tile re-stages shared memory
