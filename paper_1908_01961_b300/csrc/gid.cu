@@ -45,6 +45,7 @@ struct gid_ctx {
   int apply_th = 4;        // rows per operator tile (gid_set_apply_tile / gid_autotune)
   int pcg_blocks = 0;      // > 0: run the PCG loop as one cooperative launch of this many blocks
   int upd_cap = 148 * 4;   // vector-step blocks resident at once (SMs x blocks per SM)
+  int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
   // CUDA graphs of gid_run's launch sequence, replayed on a context-owned stream
   struct Graph {
@@ -158,7 +159,12 @@ static Params params(const gid_ctx* c) {
 }
 
 static dim3 pix_grid(const gid_ctx* c) { return dim3((c->W + BX - 1) / BX, (c->H + BY - 1) / BY); }
-static int dense_blocks(const gid_ctx* c) { return std::max(1, std::min(c->H, 296)); }
+// Blocks per colour channel of the base-colour step: the three channels
+// together fill one wave of resident blocks, each streaming its share of the
+// pitched planes as float4.
+static int dense_blocks(const gid_ctx* c) {
+  return (int)std::max(1L, std::min((c->plane / 4 + 255) / 256, (long)std::max(1, c->dense_cap / 3)));
+}
 // Blocks of the PCG operator step for the context's tile shape.
 static int apply_blocks(const gid_ctx* c) { return ((c->W + VTW - 1) / VTW) * ((c->H + c->apply_th - 1) / c->apply_th); }
 // Blocks of the PCG vector step: exactly the blocks that are resident at once
@@ -244,6 +250,16 @@ struct Launch {
       return 0;
     return coop ? sms * per_sm : 0;
   }
+  // Resident blocks of the base-colour step on this device (SMs x blocks per SM).
+  static int dense_capacity(const gid_ctx*) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_dense<K, true>, 256, 0) != cudaSuccess ||
+        per_sm < 1 || sms < 1)
+      return 148;
+    return std::min(sms * per_sm, 148 * 8);
+  }
   // Resident blocks of the vector step on this device (SMs x blocks per SM).
   static int update_capacity(const gid_ctx*) {
     int dev = 0, sms = 0, per_sm = 0;
@@ -258,7 +274,7 @@ struct Launch {
     launch_pdl(c, k_update<K>, dim3(update_blocks(c)), dim3(256), 0, params(c), it, apply_blocks(c), p, last);
   }
   static void dense(const gid_ctx* c, int solve) {
-    k_dense<K><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
+    k_dense<K, true><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
   }
   static void energy(const gid_ctx* c) { k_energy<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void init_cold(const gid_ctx* c) { k_init_cold<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
@@ -371,10 +387,7 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V + coef_planes(K, w->n_spatial_pairs);
   const size_t fbytes = (size_t)nplanes * c->plane * sizeof(float) + 256 * (size_t)nplanes;
   const size_t lbytes = ((size_t)c->plane + 255) / 256 * 256;
-  const long nb = std::max((long)pix_grid(c).x * pix_grid(c).y, (long)((W + VTW - 1) / VTW) * ((H + 1) / 2));
-  const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
-  const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
-  const size_t pbytes = (size_t)npart * sizeof(double);
+  // launch shapes that size the reduction buffers below
   switch (c->K) {
     case 1: c->upd_cap = Launch<1>::update_capacity(c); break;
     case 2: c->upd_cap = Launch<2>::update_capacity(c); break;
@@ -387,7 +400,23 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
     case 9: c->upd_cap = Launch<9>::update_capacity(c); break;
     default: c->upd_cap = Launch<10>::update_capacity(c); break;
   }
+  switch (c->K) {
+    case 1: c->dense_cap = Launch<1>::dense_capacity(c); break;
+    case 2: c->dense_cap = Launch<2>::dense_capacity(c); break;
+    case 3: c->dense_cap = Launch<3>::dense_capacity(c); break;
+    case 4: c->dense_cap = Launch<4>::dense_capacity(c); break;
+    case 5: c->dense_cap = Launch<5>::dense_capacity(c); break;
+    case 6: c->dense_cap = Launch<6>::dense_capacity(c); break;
+    case 7: c->dense_cap = Launch<7>::dense_capacity(c); break;
+    case 8: c->dense_cap = Launch<8>::dense_capacity(c); break;
+    case 9: c->dense_cap = Launch<9>::dense_capacity(c); break;
+    default: c->dense_cap = Launch<10>::dense_capacity(c); break;
+  }
   cudaGetLastError();
+  const long nb = std::max((long)pix_grid(c).x * pix_grid(c).y, (long)((W + VTW - 1) / VTW) * ((H + 1) / 2));
+  const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
+  const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
+  const size_t pbytes = (size_t)npart * sizeof(double);
   c->nbmax = (int)std::max({(long)update_blocks(c), (long)((W + VTW - 1) / VTW) * ((H + 1) / 2), 148L * 32});
   const size_t ppbytes = sizeof(double) * 4 * (size_t)c->nbmax;
   c->pool_bytes = fbytes + lbytes + 256 * 9 + sizeof(DevColors) + sizeof(DevScalars) + pbytes + ppbytes;

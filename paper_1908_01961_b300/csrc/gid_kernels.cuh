@@ -1102,10 +1102,12 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
 // normal matrix A_c = l_data sum_x R_c^2 T_k T_l + (l_IR + l_CR) I and
 // g_c = l_data sum_x R_c T_k e_c, e_c the data residual at the initial colours;
 // the last block solves the three SPD systems by FP64 Cholesky and sets
-// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel, blocks
-// stride over rows; 256 threads.
+// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel; 256
+// threads.
 // Partials: (K (K + 1) / 2 + K) values x (3 nblk) blocks doubles, value-major.
-template <int K>
+// VEC: the planes are pitched (pitch a multiple of 4, zero padding) and are
+// streamed as float4 by a grid-stride loop; otherwise blocks stride over rows.
+template <int K, bool VEC>
 __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
   constexpr int NA = K * (K + 1) / 2, NACC = NA + K, NW = 8;
   __shared__ ColorTable<K> ct;
@@ -1116,17 +1118,13 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
   float acc[NACC];
 #pragma unroll
   for (int i = 0; i < NACC; i++) acc[i] = 0.f;
-  for (int y = blockIdx.x; y < P.H; y += gridDim.x)
-    for (int x = threadIdx.x; x < P.W; x += blockDim.x) {
-    const long o = off2(P, y, x);
-    const float R = expf(P.X[c * P.plane + o]);
-    float T[K + 1];
-#pragma unroll
-    for (int k = 0; k <= K; k++) T[k] = P.X[(3 + k) * P.plane + o];
+  // one pixel: residual e = I_c - R_c sum_k b_init,kc T_k, a_k = R_c T_k (k >= 1)
+  auto pixel = [&](float r, const float* T, float I) {
+    const float R = expf(r);
     float S0 = 0.f;
 #pragma unroll
     for (int k = 0; k <= K; k++) S0 += ct.bi[k][c] * T[k];
-    const float e = P.I[c * P.plane + o] - R * S0;
+    const float e = I - R * S0;
     float a[K];
 #pragma unroll
     for (int k = 0; k < K; k++) a[k] = R * T[k + 1];
@@ -1137,7 +1135,42 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
       for (int l = 0; l <= k; l++) acc[n++] += a[k] * a[l];
 #pragma unroll
     for (int k = 0; k < K; k++) acc[NA + k] += a[k] * e;
+  };
+  if (VEC) {
+    // whole pitched planes as float4 (padding columns are zero: r = 0, T = 0, I = 0
+    // contribute nothing), a grid-stride loop of one wave
+    const long n4 = P.plane >> 2;
+    const float4* __restrict__ X4 = reinterpret_cast<const float4*>(P.X);
+    const float4* __restrict__ I4 = reinterpret_cast<const float4*>(P.I);
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += (long)gridDim.x * blockDim.x) {
+      const float4 r4 = X4[c * n4 + i], i4 = I4[c * n4 + i];
+      float4 t4[K + 1];
+#pragma unroll
+      for (int k = 0; k <= K; k++) t4[k] = X4[(3 + k) * n4 + i];
+      float T[K + 1];
+#pragma unroll
+      for (int k = 0; k <= K; k++) T[k] = t4[k].x;
+      pixel(r4.x, T, i4.x);
+#pragma unroll
+      for (int k = 0; k <= K; k++) T[k] = t4[k].y;
+      pixel(r4.y, T, i4.y);
+#pragma unroll
+      for (int k = 0; k <= K; k++) T[k] = t4[k].z;
+      pixel(r4.z, T, i4.z);
+#pragma unroll
+      for (int k = 0; k <= K; k++) T[k] = t4[k].w;
+      pixel(r4.w, T, i4.w);
     }
+  } else {
+    for (int y = blockIdx.x; y < P.H; y += gridDim.x)
+      for (int x = threadIdx.x; x < P.W; x += blockDim.x) {
+        const long o = off2(P, y, x);
+        float T[K + 1];
+#pragma unroll
+        for (int k = 0; k <= K; k++) T[k] = P.X[(3 + k) * P.plane + o];
+        pixel(P.X[c * P.plane + o], T, P.I[c * P.plane + o]);
+      }
+  }
   // block reduction: FP32 warp shuffles, then the 8 warp sums in order
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll

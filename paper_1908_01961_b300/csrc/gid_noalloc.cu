@@ -91,7 +91,7 @@ static int scratch_address(const ErrOut& eo, char** out) {
 
 template <int K>
 static void launch_dense(const Params& P, int nblk, cudaStream_t s) {
-  k_dense<K><<<dim3(nblk, 3), 256, 0, s>>>(P, 1);
+  k_dense<K, false><<<dim3(nblk, 3), 256, 0, s>>>(P, 1);
 }
 
 extern "C" int gid_dense_refine_noalloc(int H, int W, int K, const float* X_dev, const float* rgb_dev,
