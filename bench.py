@@ -176,10 +176,10 @@ def algorithmic_bytes(kind, K, P, M, ns, nt, temporal):
     if kind == "pcg":       # the persistent loop: M operator phases and M vector phases
         return M * (algorithmic_bytes("apply", K, P, M, ns, nt, temporal) +
                     algorithmic_bytes("update", K, P, M, ns, nt, temporal))
-    if kind == "update":    # read delta, p, q, r, M^-1; write delta, r, z (last: read delta, p, X; write X)
-        return 4.0 * P * ((M - 1) * 8 * V + 4 * V) / M
-    if kind == "linearize":  # read X, I, w_SR, pairs (+ r_prev, temporal sum); write M^-1, r, z, delta, coefficients
-        return 4.0 * P * (5 * V + 4 + ns + (nt + 3 + 1) * t + NC) + P
+    if kind == "update":    # read delta, p, q, z, M^-1; write delta, z (last: read delta, p, X; write X)
+        return 4.0 * P * ((M - 1) * 7 * V + 4 * V) / M
+    if kind == "linearize":  # read X, I, w_SR, pairs (+ r_prev, temporal sum); write M^-1, z, delta, coefficients
+        return 4.0 * P * (4 * V + 4 + ns + (nt + 3 + 1) * t + NC) + P
     if kind == "dense":     # read X and I
         return 4.0 * P * (V + 3)
     return None

@@ -28,7 +28,7 @@ struct gid_ctx {
   float *I = nullptr, *C = nullptr, *Cprev = nullptr, *rprev = nullptr, *wsr = nullptr, *ws = nullptr, *wt = nullptr,
         *wtsum = nullptr;
   uint8_t* lab = nullptr;
-  float *X = nullptr, *d = nullptr, *r = nullptr, *z = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr,
+  float *X = nullptr, *d = nullptr, *z = nullptr, *pA = nullptr, *pB = nullptr, *q = nullptr,
         *Minv = nullptr, *coef = nullptr;
   DevColors* col = nullptr;
   DevScalars* sc = nullptr;
@@ -145,7 +145,6 @@ static Params params(const gid_ctx* c) {
   }
   P.X = c->X;
   P.d = c->d;
-  P.r = c->r;
   P.z = c->z;
   P.q = c->q;
   P.Minv = c->Minv;
@@ -383,8 +382,8 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->pitch = (W + 31) / 32 * 32;
   c->plane = (long)H * c->pitch;
   const int ns = std::max(1, w->n_spatial_pairs), nt = std::max(1, w->n_temporal_pairs);
-  // planes: I 3, C 3, Cprev 3, rprev 3, wsr 1, ws ns, wt nt, wtsum 1, X d r z pA pB q Minv 8V, coefficients
-  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 8L * c->V + coef_planes(K, w->n_spatial_pairs);
+  // planes: I 3, C 3, Cprev 3, rprev 3, wsr 1, ws ns, wt nt, wtsum 1, X d z pA pB q Minv 7V, coefficients
+  const long nplanes = 3 + 3 + 3 + 3 + 1 + ns + nt + 1 + 7L * c->V + coef_planes(K, w->n_spatial_pairs);
   const size_t fbytes = (size_t)nplanes * c->plane * sizeof(float) + 256 * (size_t)nplanes;
   const size_t lbytes = ((size_t)c->plane + 255) / 256 * 256;
   // launch shapes that size the reduction buffers below
@@ -442,7 +441,6 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->wtsum = planes(1);
   c->X = planes(c->V);
   c->d = planes(c->V);
-  c->r = planes(c->V);
   c->z = planes(c->V);
   c->pA = planes(c->V);
   c->pB = planes(c->V);

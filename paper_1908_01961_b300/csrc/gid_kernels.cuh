@@ -66,7 +66,6 @@ struct Params {
   int off_t[2 * GID_MAX_PAIRS];
   float* X;
   float* d;
-  float* r;
   float* z;
   float* q;
   float* Minv;
@@ -465,9 +464,10 @@ __device__ __forceinline__ void load_state(const Params& P, const ColorTable<K>&
   }
 }
 
-// Linearisation (fused): g = -J^T F, diag(J^T J); PCG start r = g, z = M^-1 r;
+// Linearisation (fused): g = -J^T F, diag(J^T J); PCG start z = M^-1 g (the
+// residual r = g itself is not stored);
 // the operator coefficients of the step (CoefLayout) in every mode.
-// mode 0: PCG init (writes r, z, Minv, zero delta, rho); mode 1: stage output
+// mode 0: PCG init (writes z, Minv, zero delta, rho); mode 1: stage output
 // (writes g to gout and diag to dout); mode 2: coefficients only.
 template <int K>
 __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __restrict__ gout,
@@ -596,7 +596,6 @@ __global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __r
         const float mi = 1.0f / dg[v];
         const float zz = mi * g[v];
         P.Minv[ov] = mi;
-        P.r[ov] = g[v];
         P.z[ov] = zz;
         P.d[ov] = 0.f;
         rz += g[v] * zz;
@@ -922,8 +921,8 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
 
 // ---------------------------------------------------------------- PCG vector step
 
-// PCG vector step it: alpha = rho / <p, q>; delta += alpha p, r -= alpha q,
-// z = M^-1 r, block partials of rho' = <r, z>.
+// PCG vector step it: alpha = rho / <p, q>; delta += alpha p, z -= alpha M^-1 q
+// (the residual r = z / M^-1 is never stored), block partials of rho' = <r, z>.
 // last 1: X += delta + alpha p (the Gauss-Newton update); last 2: write delta
 // only.  Works on whole pitched planes as float4 (the padding columns of every
 // PCG vector are zero and stay zero).  A grid of a few blocks per SM strides
@@ -936,7 +935,6 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
   const long n4 = P.plane >> 2, total = (long)V * n4;
   const float4* __restrict__ p4 = reinterpret_cast<const float4*>(p);
   float4* __restrict__ d4 = reinterpret_cast<float4*>(P.d);
-  float4* __restrict__ r4 = reinterpret_cast<float4*>(P.r);
   float4* __restrict__ z4 = reinterpret_cast<float4*>(P.z);
   float4* __restrict__ X4 = reinterpret_cast<float4*>(P.X);
   const float4* __restrict__ q4 = reinterpret_cast<const float4*>(P.q);
@@ -963,9 +961,11 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
         if (o < total) d4[o] = axpy(alpha, p4[o], d4[o]);
       }
     } else {
-      // delta, r and M^-1 are touched only here: stream them past L2 (evict first) so
-      // that z, p, q and the coefficient planes the operator step re-reads stay resident.
-      float4 pv[UF], dv[UF], qv[UF], rv[UF], mv[UF];
+      // The residual r is not stored: z = M^-1 r is updated directly,
+      // z' = z - alpha M^-1 q (= M^-1 (r - alpha q)), and rho' = <r', z'> =
+      // sum z'^2 / M^-1.  delta and M^-1 are touched only here: stream them past
+      // L2 (evict first) so that z, p, q and the coefficient planes stay resident.
+      float4 pv[UF], dv[UF], qv[UF], zv[UF], mv[UF];
 #pragma unroll
       for (int u = 0; u < UF; u++) {
         const long o = base + u * stride;
@@ -973,7 +973,7 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
           pv[u] = p4[o];
           dv[u] = __ldcs(d4 + o);
           qv[u] = q4[o];
-          rv[u] = __ldcs(r4 + o);
+          zv[u] = z4[o];
           mv[u] = __ldcs(m4 + o);
         }
       }
@@ -982,11 +982,13 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
         const long o = base + u * stride;
         if (o < total) {
           __stcs(d4 + o, axpy(alpha, pv[u], dv[u]));
-          const float4 rn = axpy(-alpha, qv[u], rv[u]);
-          const float4 zz = make_float4(mv[u].x * rn.x, mv[u].y * rn.y, mv[u].z * rn.z, mv[u].w * rn.w);
-          __stcs(r4 + o, rn);
-          z4[o] = zz;
-          rz += rn.x * zz.x + rn.y * zz.y + rn.z * zz.z + rn.w * zz.w;
+          const float4 m = mv[u], q = qv[u], z = zv[u];
+          const float4 zn = make_float4(fmaf(-alpha, m.x * q.x, z.x), fmaf(-alpha, m.y * q.y, z.y),
+                                        fmaf(-alpha, m.z * q.z, z.z), fmaf(-alpha, m.w * q.w, z.w));
+          z4[o] = zn;
+          // padding entries have M^-1 = 0 and z = 0: they add nothing
+          rz += (m.x > 0.f ? zn.x * zn.x / m.x : 0.f) + (m.y > 0.f ? zn.y * zn.y / m.y : 0.f) +
+                (m.z > 0.f ? zn.z * zn.z / m.z : 0.f) + (m.w > 0.f ? zn.w * zn.w / m.w : 0.f);
         }
       }
     }
@@ -994,8 +996,8 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
   return rz;
 }
 
-// PCG vector step it: alpha = rho / <p, q>; delta += alpha p, r -= alpha q,
-// z = M^-1 r, block partials of rho' = <r, z>.  last 1: X += delta + alpha p
+// PCG vector step it: alpha = rho / <p, q>; delta += alpha p, z -= alpha M^-1 q,
+// block partials of rho' = <r, z> = sum z^2 / M^-1.  last 1: X += delta + alpha p
 // (the Gauss-Newton update); last 2: write delta only.  Works on whole pitched
 // planes as float4 (the padding columns of every PCG vector are zero and stay
 // zero).  A grid of a few blocks per SM strides over all V x plane / 4 float4
