@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--tile", type=int, default=None, choices=[0, 2, 4, 8, 17],
                     help="operator tile rows instead of autotuning (0 = persistent PCG kernel); for profiling")
-    ap.add_argument("--workload", default="video", choices=["video", "batch"],
+    ap.add_argument("--workload", default="video", choices=["video", "batch", "stream"],
                     help="video: the 640x480 K=6 video (default); batch: 24 uneven videos in one graph per step")
     return ap.parse_args()
 
@@ -303,10 +303,23 @@ def run_gid(args, ws, rank, local):
     traffic = ncu_traffic(kernel_name) if kernel_name else None
     roof = None
     if alg:
-        ach = alg / (dom_ms / 1000.0) / 1e9
+        # The profiled step launches kernel by kernel with an event after each
+        # (no graph replay, no programmatic overlap), so it runs slower than the
+        # timed steps.  Per-launch time of the dominant kernel: its share of the
+        # profiled step times the timed step's own duration, over its launches;
+        # the raw profiled figure is reported beside it.
+        prof_total = sum(v[0] for v in kinds.values())
+        step_ms = total_ms / args.steps
+        dom_scaled = dom_ms * step_ms / prof_total
+        ach = alg / (dom_scaled / 1000.0) / 1e9
+        ach_prof = alg / (dom_ms / 1000.0) / 1e9
         roof = {"bound": "hbm", "kernel": kernel_name, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": ach / peak, "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_ms}
+                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_scaled,
+                "avg_launch_ms_profiled": dom_ms, "frac_profiled": ach_prof / peak,
+                "method": "avg_launch_ms = (kernel's share of a profiled step with a CUDA event after every "
+                          "kernel) x (timed step duration) / launches; *_profiled = the profiled step's own "
+                          f"per-launch time (profiled step {prof_total:.1f} ms vs timed step {step_ms:.1f} ms)"}
     shares = {k: {"ms_per_step": v[0], "launches": v[1]} for k, v in kinds.items()}
 
     # end to end: the host-buffer entry point, host<->device copies inside the timed region
@@ -525,6 +538,93 @@ def run_batch(args, ws, rank, local):
         print(json.dumps(out), flush=True)
 
 
+# ---------------------------------------------------------------- long stream (1080p)
+
+STREAM = synth.STREAM_1080P
+STREAM_FRAMES = 60
+
+
+def _stream_frame(args):
+    seed, t = args
+    v = synth.SyntheticVideo(STREAM["H"], STREAM["W"], STREAM["K"], STREAM["n_cells"], seed=seed)
+    f = v.frame(t)
+    return f.I.astype(np.float32), f.labels
+
+
+def run_stream(args, ws, rank, local):
+    """Per-frame latency of a 1920x1080 K=8 stream: frame 0 cold, then warm
+    starts with temporal pairs, 8 GN x 20 PCG per frame.  Every frame's solve
+    (ingest, initialisation, run) is bracketed by CUDA events on the solver's
+    stream; the inputs are resident in HBM."""
+    import multiprocessing as mp
+    F = args.frames if args.frames != WORK["frames"] else STREAM_FRAMES
+    seed = 7 + rank
+    with mp.get_context("spawn").Pool(max(1, min(F, (os.cpu_count() or 2) - 1))) as pool:
+        made = pool.map(_stream_frame, [(seed, t) for t in range(F)])   # before any CUDA call
+
+    import torch
+
+    from paper_1908_01961_b300 import gid
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    H, W, K, N, M = STREAM["H"], STREAM["W"], STREAM["K"], STREAM["N"], STREAM["M"]
+    b0 = synth.initial_base_colors(made[0][0].astype(np.float64), made[0][1], K).astype(np.float32)
+    off_s, off_t = synth.offsets_for(seed)
+    rgb = [torch.from_numpy(I).to(dev) for I, _ in made]
+    lab = [torch.from_numpy(l).to(dev) for _, l in made]
+    s = gid.Solver(H, W, K, gid.default_weights(off_s, off_t, temporal=1))
+    s.set_base_colors(b0)
+    stream = torch.cuda.current_stream()
+    s.set_frame(rgb[0], lab[0])
+    s.init(0)
+    tile_rows, tile_us = s.autotune(5)
+
+    def frame(t):
+        s.set_frame(rgb[t], lab[t])
+        s.init(0 if t == 0 else 1)
+        s.run(N, M)
+
+    for _ in range(args.warmup):
+        s.new_sequence()
+        frame(0)
+    torch.cuda.synchronize()
+    s.new_sequence()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(F)]
+    barrier(ws)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    n0 = s.launch_count()
+    for t in range(F):
+        ev[t][0].record(stream)
+        frame(t)
+        ev[t][1].record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    launches = s.launch_count() - n0
+    clk = clocks.stop()
+    lat = np.array([a.elapsed_time(b) for a, b in ev])
+    total_ms = max_over_ranks(ws, float(lat.sum()))
+    E, _ = s.energy()
+    if not np.isfinite(E):
+        raise RuntimeError("non-finite energy after the stream")
+    if rank == 0:
+        out = {"metric": "per-frame latency of a 1920x1080 K=8 stream (8 GN x 20 PCG per frame)",
+               "value": float(np.percentile(lat, 50)), "unit": "ms", "n_gpus": ws, "steps": 1,
+               "warmup": args.warmup, "ms_per_step": total_ms, "higher_is_better": False, "scaling": "weak",
+               "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+               "config": {"workload": f"stream_1920x1080_K8: {F} frames, 80 moving Voronoi cells, rotating light; "
+                                      "frame 0 cold, then warm starts with temporal pairs", "H": H, "W": W, "K": K,
+                          "frames": F, "N_outer": N, "M_inner": M,
+                          "operator_tile": f"128x{tile_rows} (autotuned; us per PCG step {tile_us})",
+                          "l2": "inputs (20 MB per frame of planes, 190 MB per PCG vector set) exceed the L2"},
+               "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
+                              "max": float(lat.max()), "first_frame": float(lat[0])},
+               "frames_per_s": ws * F / (total_ms / 1000.0), "gpu_launches": launches, "e2e": None,
+               "cpu_baseline": None, "clocks": clk, "final_energy": E}
+        print(json.dumps(out), flush=True)
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -532,6 +632,8 @@ def main():
         run_reference(args, ws, rank)
     elif args.workload == "batch":
         run_batch(args, ws, rank, local)
+    elif args.workload == "stream":
+        run_stream(args, ws, rank, local)
     else:
         run_gid(args, ws, rank, local)
     if ws > 1:

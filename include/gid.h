@@ -331,8 +331,11 @@ int gid_init_learned(gid_ctx* ctx, gid_net* net, float zero_below);
 /* Number of kernels this context has launched since gid_create. */
 int gid_launch_count(const gid_ctx* ctx, long long* n);
 
-/* enable != 0: bracket every later kernel launch with CUDA events on the
- * context stream (up to 16384 launches between reads); 0 stops recording. */
+/* enable != 0: record a CUDA event on the context stream before the first and
+ * after every later kernel launch (up to 16384 launches between reads); each
+ * kernel is timed from the previous kernel's end event to its own, its launch
+ * gap included, so the kernels partition the profiled time.  Profiled runs
+ * launch kernel by kernel (no graph replay).  0 stops recording. */
 int gid_profile(gid_ctx* ctx, int enable);
 
 /* Synchronise and return, per kind, the summed device time (ms[GID_NUM_KINDS])

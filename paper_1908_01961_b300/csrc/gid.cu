@@ -1,5 +1,7 @@
 // C ABI of the illumination decomposition solver: context, buffers, launch
 // sequence.  See include/gid.h for the contract of every entry point.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -8,6 +10,7 @@
 #include <cstddef>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -53,6 +56,15 @@ struct gid_ctx {
     cudaGraphExec_t exec;
     long long kernels;
   };
+  // TMA tensor maps of a staged PCG vector per (base pointer, tile rows):
+  // boxes [3][rows + 6][136] (reflectance) and [K + 1][rows + 2][136] (layers)
+  struct Maps {
+    const float* base;
+    int th;
+    CUtensorMap r, t;
+  };
+  std::vector<Maps> maps;
+  bool map_failed = false;  // a tensor map could not be encoded (the launch was skipped)
   bool use_graph = true;
   std::vector<Graph> graphs;
   cudaStream_t gs = nullptr;
@@ -60,7 +72,7 @@ struct gid_ctx {
   // optional per-kernel CUDA-event timing (gid_profile)
   bool prof = false;
   std::vector<cudaEvent_t> ev;
-  std::vector<int> ev_kind;  // kind of each (start, end) pair
+  std::vector<int> ev_kind;  // kind of the kernel that ends at event i + 1
   double prof_ms[GID_NUM_KINDS] = {0};
   long long prof_n[GID_NUM_KINDS] = {0};
   std::string err;
@@ -88,10 +100,13 @@ static int fail(gid_ctx* ctx, int code, const char* what, const char* detail = n
 template <class F>
 static void launch(gid_ctx* c, int kind, F f) {
   const size_t i = c->ev_kind.size();
-  if (c->prof && 2 * i + 1 < c->ev.size()) {
-    cudaEventRecord(c->ev[2 * i], c->stream);
+  if (c->prof && i + 1 < c->ev.size()) {
+    // a chain of events: one before the first kernel, one after each kernel, so
+    // that each kernel owns the time since the previous one ended (its launch
+    // gap included) and the kernels partition the profiled time exactly
+    if (i == 0) cudaEventRecord(c->ev[0], c->stream);
     f();
-    cudaEventRecord(c->ev[2 * i + 1], c->stream);
+    cudaEventRecord(c->ev[i + 1], c->stream);
     c->ev_kind.push_back(kind);
   } else {
     f();
@@ -174,6 +189,46 @@ static int update_blocks(const gid_ctx* c) {
   return (int)std::max(1L, std::min((items + 255) / 256, (long)c->upd_cap));
 }
 
+// ---------------------------------------------------------------- TMA tensor maps
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// Tensor maps of the V planes at `base` (pitched like every context plane) for
+// an operator tile of `th` rows; nullptr if the driver cannot encode them.
+static const gid_ctx::Maps* tile_maps(gid_ctx* c, const float* base, int th) {
+  for (const auto& m : c->maps)
+    if (m.base == base && m.th == th) return &m;
+  auto fn = encode_fn();
+  if (!fn) return nullptr;
+  gid_ctx::Maps m;
+  m.base = base;
+  m.th = th;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->H, (cuuint64_t)c->V};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(float), (cuuint64_t)c->plane * sizeof(float)};
+  const cuuint32_t box_r[3] = {(cuuint32_t)VRW, (cuuint32_t)(th + 2 * AHR), 3u};
+  const cuuint32_t box_t[3] = {(cuuint32_t)VRW, (cuuint32_t)(th + 2), (cuuint32_t)(c->K + 1)};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  auto enc = [&](CUtensorMap* map, const cuuint32_t* box) {
+    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+  };
+  if (!enc(&m.r, box_r) || !enc(&m.t, box_t)) return nullptr;
+  c->maps.push_back(m);
+  return &c->maps.back();
+}
+
 // ---------------------------------------------------------------- K dispatch
 
 template <int K>
@@ -203,8 +258,13 @@ struct Launch {
   static void apply_th(const gid_ctx* c, int mode, int first, int it, const float* pin, float* pout, float* qout) {
     const size_t smem = sizeof(ApplyTile<K, TH>);
     const dim3 grid((c->W + VTW - 1) / VTW, (c->H + TH - 1) / TH);
+    const gid_ctx::Maps* m = tile_maps(const_cast<gid_ctx*>(c), mode == 0 ? c->z : pin, TH);
+    if (!m) {  // reported by the caller's launch check
+      const_cast<gid_ctx*>(c)->map_failed = true;
+      return;
+    }
     launch_pdl(c, k_apply<K, TH>, grid, dim3(BX, TH), smem, params(c), mode, first, it, update_blocks(c), pin, pout,
-               qout);
+               qout, m->r, m->t);
   }
   // Opt every operator tile shape in to its dynamic shared memory (before any graph capture).
   static void prepare(const gid_ctx*) {
@@ -301,6 +361,10 @@ struct Launch {
 static int check_launch(gid_ctx* c, const char* what) {
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, what, cudaGetErrorString(e));
+  if (c->map_failed) {
+    c->map_failed = false;
+    return fail(c, GID_ERR_CUDA, what, "TMA tensor map of the operator tile could not be encoded");
+  }
   return GID_OK;
 }
 
@@ -458,6 +522,11 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
     return fail(nullptr, GID_ERR_OOM, "internal pool layout");
   }
   GID_DISPATCH(c, prepare, c);
+  if (!tile_maps(c, c->z, c->apply_th)) {
+    cudaFree(c->pool);
+    delete c;
+    return fail(nullptr, GID_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed for the operator tile");
+  }
   switch (c->K) {
     case 1: c->pcg_blocks = Launch<1>::pcg_capacity(c); break;
     case 2: c->pcg_blocks = Launch<2>::pcg_capacity(c); break;
@@ -872,7 +941,7 @@ extern "C" int gid_launch_count(const gid_ctx* c, long long* n) {
 extern "C" int gid_profile(gid_ctx* c, int enable) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (enable && c->ev.empty()) {
-    c->ev.resize(2 * 16384);
+    c->ev.resize(16384 + 1);
     for (auto& e : c->ev) GID_TRY_CUDA(c, cudaEventCreate(&e));
   }
   c->prof = enable != 0;
@@ -884,7 +953,7 @@ extern "C" int gid_profile_read(gid_ctx* c, double* ms, long long* count) {
   GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
   for (size_t i = 0; i < c->ev_kind.size(); i++) {
     float t = 0.f;
-    GID_TRY_CUDA(c, cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]));
+    GID_TRY_CUDA(c, cudaEventElapsedTime(&t, c->ev[i], c->ev[i + 1]));
     c->prof_ms[c->ev_kind[i]] += t;
     c->prof_n[c->ev_kind[i]]++;
   }

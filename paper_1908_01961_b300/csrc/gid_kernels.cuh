@@ -16,6 +16,7 @@
 // frame runs without a host round trip.
 #pragma once
 
+#include <cuda.h>  // CUtensorMap
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -48,7 +49,9 @@ struct DevScalars {
   unsigned int cnt[8];
   int status;
 };
-enum { CNT_LIN, CNT_APPLY, CNT_UPDATE, CNT_DENSE, CNT_ENERGY, CNT_GRID, CNT_GEN };
+// arrival counters: linearisation, base-colour step per colour channel (3),
+// energy, persistent-kernel grid barrier (count, generation)
+enum { CNT_LIN, CNT_DENSE, CNT_ENERGY = CNT_DENSE + 3, CNT_GRID, CNT_GEN };
 
 struct Params {
   int H, W, pitch;
@@ -119,12 +122,12 @@ __device__ __forceinline__ double block_sum_f(float v) {
 
 // True in every thread of the last block to arrive.  Thread 0 must have
 // written this block's partials before the call.  Resets the counter.
-__device__ __forceinline__ bool last_block(unsigned int* cnt) {
+__device__ __forceinline__ bool last_block(unsigned int* cnt, unsigned int n = 0u) {
   __shared__ bool is_last;
   __threadfence();
   __syncthreads();
   if (tid_flat() == 0) {
-    const unsigned int n = gridDim.x * gridDim.y * gridDim.z;
+    if (n == 0u) n = gridDim.x * gridDim.y * gridDim.z;
     const unsigned int t = atomicAdd(cnt, 1u);
     is_last = (t == n - 1);
     if (is_last) *cnt = 0u;
@@ -470,7 +473,7 @@ __device__ __forceinline__ void load_state(const Params& P, const ColorTable<K>&
 // mode 0: PCG init (writes z, Minv, zero delta, rho); mode 1: stage output
 // (writes g to gout and diag to dout); mode 2: coefficients only.
 template <int K>
-__global__ void __launch_bounds__(NT) k_linearize(Params P, int mode, float* __restrict__ gout,
+__global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int mode, float* __restrict__ gout,
                                                   float* __restrict__ dout) {
   constexpr int V = K + 4;
   __shared__ ColorTable<K> ct;
@@ -657,10 +660,12 @@ __device__ __forceinline__ F4 lds4(const float* p) { return f4(*reinterpret_cast
 // y0-1 .. y0+8 of the layers, columns x0-4 .. x0+131 (halo padded to a float4).
 constexpr int QW = 4, VTW = BX * QW, VHX = 4, VRW = VHX + VTW + 4, AHR = 3;
 
+// Both arrays are TMA destinations (128-byte aligned boxes: [3][TH + 6][136]
+// and [K + 1][TH + 2][136] floats).
 template <int K, int TH>
 struct ApplyTile {
-  float pr[3][TH + 2 * AHR][VRW];
-  float pt[K + 1][TH + 2][VRW];
+  alignas(128) float pr[3][TH + 2 * AHR][VRW];
+  alignas(128) float pt[K + 1][TH + 2][VRW];
 };
 
 // Apply tile shapes: TH rows of 128 pixels, a 32 x TH block, at most MAXREG
@@ -698,6 +703,47 @@ struct ApplyShape<17> {
 // p = s (+ beta p_old) on the tile's pixels.  get_beta() is called once the
 // staging loads are in (it may wait on a block reduction).  Returns this
 // thread's share of <p, q>.  All threads of the block call it.
+// ---- TMA: one elected thread copies a 3-D box of planes into shared memory,
+// completion counted in bytes on an mbarrier.
+constexpr long TMA_SPINS = 1L << 22;  // bounded wait (then ST_TIMEOUT)
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Box of the tensor map at (x, y, z) (x in elements, 16-byte aligned; may be
+// negative or past the end: those elements read as zero).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// 16-byte asynchronous global -> shared copy (L2 only); src_bytes = 0 writes
+// zeros and reads nothing.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((unsigned)__cvta_generic_to_shared(dst)),
+               "l"(src), "r"(src_bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;\n" ::: "memory"); }
+
 // Bulk prefetch of bytes [p, p + bytes) into L2 (no registers, no completion
 // to wait for); p 16-byte aligned, bytes a multiple of 16.
 __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
@@ -730,19 +776,21 @@ __device__ __forceinline__ void prefetch_tile(const Params& P, int x0, int y0, i
 __device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
 __device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory"); }
 
+// With mapR / mapT (tensor maps of the staged vector, boxes [3][TH + 6][136] and
+// [K + 1][TH + 2][136]) the tile is staged by TMA; without them (nullptr) by
+// per-thread asynchronous copies.
 template <int K, int TH, class GB>
 __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t, const ColorTable<K>& ct, int x0, int y0,
                                             int mode, int first, GB get_beta, const float* pin, float* pout,
-                                            float* __restrict__ qout) {
+                                            float* __restrict__ qout, const CUtensorMap* mapR = nullptr,
+                                            const CUtensorMap* mapT = nullptr) {
   using CL = CoefLayout<K>;
   constexpr int NCH = VRW / 4;  // float4 chunks per staged row
   constexpr int NTH = BX * TH;  // threads per block
   const int tid = tid_flat();
-  // Stage s = z (PCG step) or s = pin (stage call) with its halo.  Each thread
-  // issues up to SB chunk loads before storing any, so a block needs only a
-  // couple of memory round trips.
+  // Stage s = z (PCG step) or s = pin (stage call) with its halo.
   const float* __restrict__ sv = mode == 0 ? P.z : pin;
-  constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH, SB = TH >= 17 ? 4 : 8;
+  constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH;
   auto chunk_dst = [&](int i, int& gy, int& gx, int& v) -> float* {
     if (i < NR) {
       const int c = i / ((TH + 2 * AHR) * NCH), rem = i - c * (TH + 2 * AHR) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
@@ -757,27 +805,33 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
     v = 3 + k;
     return &t.pt[k][ly][4 * lc];
   };
-  for (int base = tid; base < NTOT; base += SB * NTH) {
-    float4 val[SB];
-#pragma unroll
-    for (int s = 0; s < SB; s++) {
-      const int i = base + s * NTH;
-      val[s] = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (i < NTOT) {
-        int gy, gx, v;
-        chunk_dst(i, gy, gx, v);
-        if (gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch)
-          val[s] = *reinterpret_cast<const float4*>(sv + v * P.plane + off2(P, gy, gx));
-      }
+  const bool use_tma = mapR != nullptr && ((smem_addr(&t.pr[0][0][0]) | smem_addr(&t.pt[0][0][0])) & 127u) == 0u;
+  if (use_tma) {
+    // two TMA boxes (reflectance channels with a 3-row halo, layers with 1),
+    // columns x0 - 4 .. x0 + 131 (x0 - 4 is a multiple of 4 floats, also when
+    // negative); outside the frame they read as zero
+    __shared__ __align__(8) uint64_t bar;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_expect_tx(&bar, (unsigned)(sizeof(t.pr) + sizeof(t.pt)));
+      tma_load_3d(&t.pr[0][0][0], mapR, x0 - VHX, y0 - AHR, 0, &bar);
+      tma_load_3d(&t.pt[0][0][0], mapT, x0 - VHX, y0 - 1, 3, &bar);
     }
-#pragma unroll
-    for (int s = 0; s < SB; s++) {
-      const int i = base + s * NTH;
-      if (i < NTOT) {
-        int gy, gx, v;
-        *reinterpret_cast<float4*>(chunk_dst(i, gy, gx, v)) = val[s];
-      }
+    bool done = false;
+    for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
+    if (!done && tid == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+  } else {
+    // Every chunk is an asynchronous 16-byte copy straight into shared memory
+    // (zero-filled outside the frame): all of a thread's copies are in flight
+    // at once and hold no registers.
+    for (int i = tid; i < NTOT; i += NTH) {
+      int gy, gx, v;
+      float* dst = chunk_dst(i, gy, gx, v);
+      const bool ok = gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch;
+      cp_async16(dst, ok ? sv + v * P.plane + off2(P, gy, gx) : sv, ok ? 16 : 0);
     }
+    cp_async_wait_all();
   }
   __syncthreads();
   const float beta = get_beta();
@@ -894,8 +948,9 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
 template <int K, int TH>
 __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     k_apply(Params P, int mode, int first, int it, int nb_prev, const float* pin, float* pout,
-            float* __restrict__ qout) {
-  extern __shared__ float4 apply_smem[];
+            float* __restrict__ qout, const __grid_constant__ CUtensorMap mapR,
+            const __grid_constant__ CUtensorMap mapT) {
+  extern __shared__ __align__(128) float4 apply_smem[];
   ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
@@ -913,7 +968,8 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     if (tid_flat() == 0 && blockIdx.x == 0 && blockIdx.y == 0) P.sc->rho2[it & 1] = rho;
     return rho_old != 0.0 ? (float)(rho / rho_old) : 0.f;
   };
-  const float pq = apply_tile<K, TH>(P, t, ct, blockIdx.x * VTW, blockIdx.y * TH, mode, first, get_beta, pin, pout, qout);
+  const float pq = apply_tile<K, TH>(P, t, ct, blockIdx.x * VTW, blockIdx.y * TH, mode, first, get_beta, pin, pout, qout,
+                                     &mapR, &mapT);
   if (mode != 0) return;
   const double bs = block_sum_f(pq);
   if (tid_flat() == 0) pcg_partials(P, PART_PQ, it)[blockIdx.y * gridDim.x + blockIdx.x] = bs;
@@ -1062,7 +1118,7 @@ __device__ __forceinline__ bool grid_sync(DevScalars* sc) {
 template <int K, int TH>
 __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     k_pcg(Params P, int m_inner, int last_mode, float* p, float* __restrict__ q) {
-  extern __shared__ float4 apply_smem[];
+  extern __shared__ __align__(128) float4 apply_smem[];
   ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
@@ -1103,8 +1159,8 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
 // Base-colour refinement (eq:basecolorrefinement): per channel c the K x K
 // normal matrix A_c = l_data sum_x R_c^2 T_k T_l + (l_IR + l_CR) I and
 // g_c = l_data sum_x R_c T_k e_c, e_c the data residual at the initial colours;
-// the last block solves the three SPD systems by FP64 Cholesky and sets
-// b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel; 256
+// the last block of each channel solves its SPD system by FP64 Cholesky and
+// sets that channel of b = b_init + Delta b.  Grid (nblk, 3): blockIdx.y is the channel; 256
 // threads.
 // Partials: (K (K + 1) / 2 + K) values x (3 nblk) blocks doubles, value-major.
 // VEC: the planes are pitched (pitch a multiple of 4, zero padding) and are
@@ -1189,20 +1245,20 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
     for (int ww = 0; ww < NW; ww++) s += wsum[ww][threadIdx.x];
     P.partial[(long)threadIdx.x * nbt + b] = s;
   }
-  if (!last_block(&P.sc->cnt[CNT_DENSE])) return;
-  // each warp sums whole (channel, value) rows: lanes stride the blocks, then a shuffle tree
-  for (int row = wid; row < 3 * NACC; row += NW) {
-    const int cc = row / NACC, i = row - cc * NACC;
-    const double* src = P.partial + (long)i * nbt + (long)cc * gridDim.x;
+  // the last block of each channel reduces and solves that channel's system
+  if (!last_block(&P.sc->cnt[CNT_DENSE + c], gridDim.x)) return;
+  // each warp sums whole value rows: lanes stride the blocks, then a shuffle tree
+  for (int i = wid; i < NACC; i += NW) {
+    const double* src = P.partial + (long)i * nbt + (long)c * gridDim.x;
     double s = 0.0;
     for (int bb = lane; bb < (int)gridDim.x; bb += 32) s += __ldcg(src + bb);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-    if (lane == 0) tot[cc][i] = s;
+    if (lane == 0) tot[c][i] = s;
   }
   __syncthreads();
-  if (threadIdx.x < 3) {
-    const int cc = threadIdx.x;
+  if (threadIdx.x == 0) {
+    const int cc = c;
     const double ld = P.w.ld, ridge = (double)P.w.lIR + (double)P.w.lCR;
     double A[K][K], L[K][K], g[K], yv[K], xs[K];
     int n = 0;
