@@ -72,6 +72,7 @@ struct gid_net {
   bf16 *gA2 = nullptr, *gB2 = nullptr, *gup2 = nullptr, *gs2 = nullptr, *gp1 = nullptr;
   bf16 *gA3 = nullptr, *gB3 = nullptr, *gup3 = nullptr, *gs3 = nullptr, *gp2 = nullptr;
   bf16 *gA4 = nullptr, *gB4 = nullptr, *gp3 = nullptr;
+  int* status = nullptr;  // device word: bit 0 = a bounded wait of the tensor-core convolution gave up
   long long launches = 0;
   long long* extra_count = nullptr;  // a solver context's launch counter during gid_init_learned
   std::string err;
@@ -108,7 +109,27 @@ static int check(gid_net* n, const char* what) {
 
 static unsigned blocks_for(long n, int t = 256) { return (unsigned)((n + t - 1) / t); }
 
+// Reads and clears the device status word (the stream must be synchronised).
+static int check_status(gid_net* n) {
+  int st = 0;
+  NET_TRY_CUDA(n, cudaMemcpy(&st, n->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (st) {
+    NET_TRY_CUDA(n, cudaMemset(n->status, 0, sizeof(int)));
+    return nfail(n, GID_ERR_TIMEOUT, "a bounded wait of the tensor-core convolution gave up");
+  }
+  return GID_OK;
+}
+
 // ---------------------------------------------------------------- launches
+
+// Pipeline depth of the tensor-core convolution for N output channels: the
+// copies are the bottleneck, so the ring is kept small enough for 3-5 CTAs
+// (12-20 copying warps) per SM (3 stages measured slower); TMEM (N columns
+// each, rounded up to a power of two) stays within the SM's 512 columns.
+static int tc_stages(int) { return 2; }
+// Its dynamic shared memory: the stages of A (128 pixels x 64 bf16) and B
+// (N x 64 bf16), plus 1 KB of slack for the 1024-byte alignment of the tiles.
+static size_t tc_smem_bytes(int N) { return (size_t)tc_stages(N) * (TC_BM * 128 + N * 128) + 1024; }
 
 static void conv(gid_net* n, const bf16* in1, int C1, int up1, const bf16* in2, int C2, const bf16* w,
                  const float* bias, int taps, int Co1, int Co2, bf16* out1, bf16* out2, float* out32,
@@ -134,11 +155,8 @@ static void conv(gid_net* n, const bf16* in1, int C1, int up1, const bf16* in2, 
   a.relu = relu;
   const long P = (long)B * H * W;
   const int Co = Co1 + Co2;
-  const unsigned gx = (unsigned)((P + CONV_BM - 1) / CONV_BM);
-  if (Co % 64 == 0)
-    k_conv<2><<<dim3(gx, Co / 64), 256, 0, n->s>>>(a);
-  else
-    k_conv<1><<<dim3(gx, Co / 32), 128, 0, n->s>>>(a);
+  const unsigned gx = (unsigned)((P + TC_BM - 1) / TC_BM);
+  k_conv_tc<2><<<gx, TC_BM, tc_smem_bytes(Co), n->s>>>(a, n->status);
   counted(n);
 }
 
@@ -440,6 +458,14 @@ extern "C" int gid_net_create(int K, const int* widths, uint64_t seed, void* str
   n->m = n->grad + off;
   n->v = n->m + off;
   if (cudaMalloc(&n->wb, 2 * sizeof(bf16) * q) != cudaSuccess) return bad("packed weights");
+  if (cudaMalloc(&n->status, sizeof(int)) != cudaSuccess || cudaMemset(n->status, 0, sizeof(int)) != cudaSuccess)
+    return bad("status word");
+  if (cudaFuncSetAttribute(k_conv_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes(256)) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    gid_net_destroy(n);
+    return nfail(nullptr, GID_ERR_CUDA, "tensor-core convolution: shared memory attribute");
+  }
   n->wt = n->wb + q;
   // He-normal weights, zero biases, from the seed
   std::vector<float> h(off, 0.f);
@@ -466,6 +492,7 @@ extern "C" void gid_net_destroy(gid_net* n) {
   cudaFree(n->wb);
   cudaFree(n->arena);
   cudaFree(n->lossp);
+  cudaFree(n->status);
   delete n;
 }
 
@@ -520,7 +547,7 @@ static int get_blob(gid_net* n, const float* dev, float* blob_host) {
   NET_TRY_CUDA(n, cudaMemcpyAsync(h.data(), dev, sizeof(float) * n->n_master, cudaMemcpyDeviceToHost, n->s));
   NET_TRY_CUDA(n, cudaStreamSynchronize(n->s));
   internal_to_blob(n, h.data(), blob_host);
-  return GID_OK;
+  return check_status(n);
 }
 
 extern "C" int gid_net_get_weights(gid_net* n, float* blob_host) { return get_blob(n, n ? n->master : nullptr, blob_host); }
@@ -571,6 +598,7 @@ extern "C" int gid_net_backward(gid_net* n, int B, int H, int W, const float* rg
   if (loss_host) {
     NET_TRY_CUDA(n, cudaMemcpyAsync(n->lossp_host.data(), n->lossp, sizeof(double) * nb, cudaMemcpyDeviceToHost, n->s));
     NET_TRY_CUDA(n, cudaStreamSynchronize(n->s));
+    if (int rc = check_status(n)) return rc;
     double t = 0.0;
     for (unsigned i = 0; i < nb; i++) t += n->lossp_host[i];
     *loss_host = t;

@@ -5,16 +5,17 @@
 // (taps = 9 for 3x3, 1 for 1x1), packed from FP32 master weights.
 //
 // A convolution is an implicit GEMM, M = pixels, N = output channels,
-// K = taps x input channels, issued as mma.sync m16n8k16 (bf16 in, fp32
-// accumulate) on tiles staged in shared memory by cp.async (double buffered)
-// and read with ldmatrix.  The input may be the channel concatenation of two
-// tensors (the decoder's skip connections), the first of them read through a
-// nearest 2x upsampling (so the upsampled tensor is never stored); the output
-// may be split into two tensors (the gradient of such a concatenation).  The
-// input gradient is the same kernel on the output gradient with the weights
-// flipped in space and transposed in channels.  The weight gradient is a GEMM
-// over pixels (M = output channels, N = taps x input channels) split across
-// blocks and reduced with FP32 atomics.
+// K = taps x input channels, on the 5th-generation tensor cores (tcgen05.mma,
+// bf16 operands in shared memory, fp32 accumulator in tensor memory; k_conv_tc
+// below).  The input may be the channel concatenation of two tensors (the
+// decoder's skip connections), the first of them read through a nearest 2x
+// upsampling (so the upsampled tensor is never stored); the output may be split
+// into two tensors (the gradient of such a concatenation).  The input gradient
+// is the same kernel on the output gradient with the weights flipped in space
+// and transposed in channels.  The weight gradient is a GEMM over pixels
+// (M = output channels, N = taps x input channels) split across blocks, on
+// warp-level mma.sync m16n8k16 tiles staged by cp.async and read with ldmatrix,
+// reduced with FP32 atomics.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -98,134 +99,213 @@ struct ConvArgs {
   int B, H, W, taps, relu;
 };
 
-constexpr int CONV_BM = 128, CONV_BK = 32, CONV_LD = CONV_BK + 8;
+// ---------------------------------------------------------------- tcgen05 convolution
+//
+// The same implicit GEMM on the 5th-generation tensor cores: D[128 pixels][N =
+// all output channels] accumulates in tensor memory (FP32, one TMEM lane per
+// pixel, one column per channel); K = taps x C_in flattened as k = tap C_in +
+// c, in chunks of 64 (one 128-byte swizzle atom of bf16).  All 128 threads
+// stage the im2col rows of A and the weight rows of B with 16-byte cp.async
+// copies into K-major, 128-byte-swizzled shared tiles (a STAGES-deep ring); one
+// thread issues tcgen05.mma kind::f16 (A and B bf16, D fp32, M = 128, K = 16
+// per instruction) and commits each stage to an mbarrier that frees it for the
+// next copies.  Waits are bounded (status bit on timeout); TMEM is allocated
+// by warp 0 (at most 256 columns; at most two CTAs fit on an SM) and always
+// freed before the CTA exits.
 
-// Block: 128 pixels x 32 WN output channels, 4 WN warps (4 along pixels, WN
-// along channels), each warp 32 pixels x 32 channels (2 x 4 mma tiles).
-// Grid (ceil(P / 128), (Co1 + Co2) / (32 WN)).
-template <int WN>
-__global__ void __launch_bounds__(128 * WN) k_conv(ConvArgs a) {
-  constexpr int NT = 128 * WN, BN = 32 * WN;
-  __shared__ __align__(16) bf16 sA[2][CONV_BM][CONV_LD];
-  __shared__ __align__(16) bf16 sB[2][BN][CONV_LD];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-  const int wm = warp & 3, wn = warp >> 2;
-  const long P = (long)a.B * a.H * a.W;
-  const long p0 = (long)blockIdx.x * CONV_BM;
-  const int co0 = blockIdx.y * BN, Ci = a.C1 + a.C2, Co = a.Co1 + a.Co2;
-  const int nchunk = (Ci + CONV_BK - 1) / CONV_BK, nsteps = a.taps * nchunk;
+constexpr int TC_BM = 128, TC_BK = 64;
+constexpr long TC_SPINS = 1L << 22;
 
-  // this thread's A rows (pixel, 16-byte chunk) for staging
-  constexpr int AJ = CONV_BM * 4 / NT;
-  Pix ap[AJ];
-  bool aok[AJ];
-#pragma unroll
-  for (int j = 0; j < AJ; j++) {
-    const long p = p0 + ((tid + j * NT) >> 2);
-    aok[j] = p < P;
-    ap[j] = pix_of(aok[j] ? p : 0, a.H, a.W);
+__device__ __forceinline__ void tc_mbar_init(uint64_t* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool tc_mbar_wait(uint64_t* bar, unsigned parity) {
+  for (long i = 0; i < TC_SPINS; i++) {
+    unsigned done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
   }
+  return false;
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 
-  auto stage = [&](int s, int buf) {
-    const int tap = s / nchunk, ci0 = (s - tap * nchunk) * CONV_BK;
-    const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle, rows of
+// 128 bytes, 8-row groups 1024 bytes apart (stride byte offset); the leading
+// byte offset is not used by this layout; descriptor version 1 (sm_100 family).
+__device__ __forceinline__ uint64_t tc_desc_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t tc_idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+template <int STAGES>
+__global__ void __launch_bounds__(128, 1) k_conv_tc(ConvArgs a, int* __restrict__ status) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_stage[STAGES];
+  __shared__ __align__(8) uint64_t bar_done;
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int N = a.Co1 + a.Co2;  // 32..256, a multiple of 32
+  const int Ci = a.C1 + a.C2, Ktot = a.taps * Ci, nk = (Ktot + TC_BK - 1) / TC_BK;
+  const uint32_t ncols = N <= 32 ? 32u : N <= 64 ? 64u : N <= 128 ? 128u : 256u;
+  const int a_bytes = TC_BM * 128, stage_bytes = a_bytes + N * 128;  // N * 128 is a multiple of 1024
+  // 1024-byte aligned ring of stages (the dynamic allocation has 1 KB of slack)
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  uint8_t* st = tc_smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t st_addr = smem_u32(st);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; i++) tc_mbar_init(&bar_stage[i]);
+    tc_mbar_init(&bar_done);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  const long P = (long)a.B * a.H * a.W, p = (long)blockIdx.x * TC_BM + tid;
+  const bool prow = p < P;
+  const Pix px = pix_of(prow ? p : 0, a.H, a.W);
+
+  // stage s <- K-chunk kc: A row `tid` (8 chunks of 8 channels), B rows of the weights
+  auto load_stage = [&](int kc, int s) {
+    uint8_t* sa = st + s * stage_bytes;
+    uint8_t* sb = sa + a_bytes;
+    // k = tap C_in + ch for the 8 chunks: one division, then wrap-arounds
+    int tap = (kc * TC_BK) / Ci, ch = kc * TC_BK - tap * Ci;
 #pragma unroll
-    for (int j = 0; j < AJ; j++) {
-      const int i = tid + j * NT, row = i >> 2, ch = ci0 + (i & 3) * 8;
-      const int yy = ap[j].y + dy, xx = ap[j].x + dx;
-      const bool ok = aok[j] && ch < Ci && yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-      const bf16* src = a.in1;
-      if (ok) {
-        if (ch < a.C1)
-          src = a.in1 + tensor_off(ap[j].b, yy, xx, a.H, a.W, a.up1, a.C1, ch);
-        else
-          src = a.in2 + tensor_off(ap[j].b, yy, xx, a.H, a.W, 0, a.C2, ch - a.C1);
+    for (int c = 0; c < 8; c++, ch += 8) {
+      while (ch >= Ci) {
+        ch -= Ci;
+        tap++;
       }
-      cp16(&sA[buf][row][(i & 3) * 8], src, ok ? 16 : 0);
+      const int k = kc * TC_BK + c * 8;
+      const bf16* src = a.in1;
+      int bytes = 0;
+      if (prow && k < Ktot) {
+        const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
+        const int yy = px.y + dy, xx = px.x + dx;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+          src = ch < a.C1 ? a.in1 + tensor_off(px.b, yy, xx, a.H, a.W, a.up1, a.C1, ch)
+                          : a.in2 + tensor_off(px.b, yy, xx, a.H, a.W, 0, a.C2, ch - a.C1);
+          bytes = 16;
+        }
+      }
+      cp16(sa + tid * 128 + ((c ^ (tid & 7)) << 4), src, bytes);
     }
-    for (int i = tid; i < BN * 4; i += NT) {
-      const int n = i >> 2, ch = ci0 + (i & 3) * 8;
-      const bool ok = ch < Ci;
-      const bf16* src = ok ? a.w + ((long)(co0 + n) * a.taps + tap) * Ci + ch : a.w;
-      cp16(&sB[buf][n][(i & 3) * 8], src, ok ? 16 : 0);
+    for (int i = tid; i < N * 8; i += TC_BM) {
+      const int r = i >> 3, c = i & 7, k = kc * TC_BK + c * 8;
+      const bool ok = k < Ktot;
+      cp16(sb + r * 128 + ((c ^ (r & 7)) << 4), ok ? a.w + (long)r * Ktot + k : a.w, ok ? 16 : 0);
     }
-    cp_commit();
   };
 
-  float acc[2][4][4];
+  const uint32_t idesc = tc_idesc_bf16(TC_BM, N);
+  bool waits_ok = true;
 #pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-#pragma unroll
-      for (int e = 0; e < 4; e++) acc[i][j][e] = 0.f;
-
-  stage(0, 0);
-  for (int s = 0; s < nsteps; s++) {
-    const int buf = s & 1;
-    if (s + 1 < nsteps) {
-      stage(s + 1, buf ^ 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k0 = 0; k0 < CONV_BK; k0 += 16) {
-      uint32_t A[2][4], Bf[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; mt++)
-        ldsm_x4(A[mt], &sA[buf][wm * 32 + mt * 16 + (lane & 15)][k0 + (lane >> 4) * 8]);
-#pragma unroll
-      for (int np = 0; np < 2; np++) {
-        uint32_t r[4];
-        ldsm_x4(r, &sB[buf][wn * 32 + np * 16 + (lane & 7) + ((lane >> 4) << 3)][k0 + ((lane >> 3) & 1) * 8]);
-        Bf[2 * np][0] = r[0];
-        Bf[2 * np][1] = r[1];
-        Bf[2 * np + 1][0] = r[2];
-        Bf[2 * np + 1][1] = r[3];
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int nt = 0; nt < 4; nt++) mma16816(acc[mt][nt], A[mt], Bf[nt]);
-    }
-    __syncthreads();
+  for (int s = 0; s < STAGES - 1; s++) {
+    if (s < nk) load_stage(s, s);
+    cp_commit();
   }
+  for (int kc = 0; kc < nk; kc++) {
+    const int s = kc % STAGES;
+    cp_wait<STAGES - 2>();  // this thread's copies of chunk kc have landed
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // ... and are visible to the tensor core
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sa = st_addr + s * stage_bytes, sb = sa + a_bytes;
+#pragma unroll
+      for (int kk = 0; kk < TC_BK / 16; kk++) {
+        const uint64_t ad = tc_desc_sw128(sa + kk * 32), bd = tc_desc_sw128(sb + kk * 32);
+        const uint32_t acc = (kc | kk) != 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&bar_stage[s]))
+                   : "memory");
+    }
+    // chunk kc + STAGES - 1 refills the stage of chunk kc - 1 once its MMAs are done
+    const int nxt = kc + STAGES - 1;
+    if (nxt < nk) {
+      const int ns = nxt % STAGES;
+      if (kc >= 1) waits_ok &= tc_mbar_wait(&bar_stage[ns], (unsigned)(((kc - 1) / STAGES) & 1));
+      load_stage(nxt, ns);
+    }
+    cp_commit();
+  }
+  if (tid == 0)
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                     smem_u32(&bar_done))
+                 : "memory");
+  waits_ok &= tc_mbar_wait(&bar_done, 0u);
+  tc_fence_after();
 
+  // epilogue: this thread's pixel is TMEM lane tid (warp w reads lanes 32 w ..)
+  const int Co = N;
+  for (int j = 0; j < N; j += 16) {
+    uint32_t r[16];
+    const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+    if (!prow) continue;
+    float v[16];
 #pragma unroll
-  for (int mt = 0; mt < 2; mt++) {
+    for (int e = 0; e < 16; e++) {
+      v[e] = __uint_as_float(r[e]) + (a.bias ? a.bias[j + e] : 0.f);
+      if (a.relu) v[e] = fmaxf(v[e], 0.f);
+    }
+    if (a.out32) {
+      float4* dst = reinterpret_cast<float4*>(a.out32 + p * Co + j);
 #pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const long p = p0 + wm * 32 + mt * 16 + g + 8 * h;
-      if (p >= P) continue;
+      for (int e = 0; e < 4; e++) dst[e] = make_float4(v[4 * e], v[4 * e + 1], v[4 * e + 2], v[4 * e + 3]);
+      continue;
+    }
+    const bool first = j < a.Co1;
+    if (first && a.mask) {
+      const uint4* mk = reinterpret_cast<const uint4*>(a.mask + p * a.Co1 + j);
+      const uint4 m0 = mk[0], m1 = mk[1];
+      const uint32_t mw[8] = {m0.x, m0.y, m0.z, m0.w, m1.x, m1.y, m1.z, m1.w};
 #pragma unroll
-      for (int nt = 0; nt < 4; nt++) {
-        const int co = co0 + wn * 32 + nt * 8 + 2 * t4;
-        float v0 = acc[mt][nt][2 * h], v1 = acc[mt][nt][2 * h + 1];
-        if (a.bias) {
-          v0 += a.bias[co];
-          v1 += a.bias[co + 1];
-        }
-        if (a.relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
-        }
-        if (a.out32) {
-          *reinterpret_cast<float2*>(a.out32 + p * Co + co) = make_float2(v0, v1);
-        } else if (co < a.Co1) {
-          if (a.mask) {
-            const __nv_bfloat162 m = *reinterpret_cast<const __nv_bfloat162*>(a.mask + p * a.Co1 + co);
-            if (!(bf(m.x) > 0.f)) v0 = 0.f;
-            if (!(bf(m.y) > 0.f)) v1 = 0.f;
-          }
-          *reinterpret_cast<uint32_t*>(a.out1 + p * a.Co1 + co) = pack2(v0, v1);
-        } else {
-          *reinterpret_cast<uint32_t*>(a.out2 + p * a.Co2 + (co - a.Co1)) = pack2(v0, v1);
-        }
+      for (int e = 0; e < 8; e++) {
+        const __nv_bfloat162 m2 = *reinterpret_cast<const __nv_bfloat162*>(&mw[e]);
+        if (!(bf(m2.x) > 0.f)) v[2 * e] = 0.f;
+        if (!(bf(m2.y) > 0.f)) v[2 * e + 1] = 0.f;
       }
     }
+    uint4* dst = first ? reinterpret_cast<uint4*>(a.out1 + p * a.Co1 + j)
+                       : reinterpret_cast<uint4*>(a.out2 + p * a.Co2 + (j - a.Co1));
+    dst[0] = make_uint4(pack2(v[0], v[1]), pack2(v[2], v[3]), pack2(v[4], v[5]), pack2(v[6], v[7]));
+    dst[1] = make_uint4(pack2(v[8], v[9]), pack2(v[10], v[11]), pack2(v[12], v[13]), pack2(v[14], v[15]));
   }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(ncols) : "memory");
+  if (!waits_ok) atomicOr(status, 1);
 }
 
 struct WgradArgs {
