@@ -144,9 +144,11 @@ class ClockSampler:
 
 
 def source_hash():
+    """Hash of the sources that define and launch the solver kernels (the ones
+    whose DRAM traffic profiles/traffic.json records)."""
     h = hashlib.sha256()
     d = os.path.join(ROOT, "paper_1908_01961_b300", "csrc")
-    for f in sorted(os.listdir(d)):
+    for f in ("gid_kernels.cuh", "gid.cu"):
         h.update(open(os.path.join(d, f), "rb").read())
     return h.hexdigest()[:16]
 

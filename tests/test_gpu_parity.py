@@ -274,3 +274,17 @@ def test_base_color_step_matches_oracle():
     s.base_color_step()
     A, g = pb.dense_normal(X)
     assert np.abs(s.base_colors() - (case.b_init + O.dense_solve(A, g))).max() <= 1e-4
+
+
+@pytest.mark.parametrize("H,W,K,n_cells", [(5, 3, 1, 2), (9, 7, 2, 3), (30, 40, 10, 14)])
+def test_end_to_end_edge_shapes(H, W, K, n_cells):
+    """Degenerate and extreme cases at the solver's bar: a single base colour
+    (K = 1, every indirect layer is zero), frames smaller than one operator tile
+    and than the consistency pairs' reach in both directions (most pairs fall
+    outside), and the maximum K = 10."""
+    case = Case(H=H, W=W, K=K, n_cells=n_cells, seed=2)
+    (R, T, b, E), (Ro, To, bo, Eo) = run_both(case, 3, 8)
+    assert np.abs(R - Ro).max() <= 1e-3
+    assert np.abs(T - To).max() <= 1e-3
+    assert np.abs(b - bo).max() <= 1e-3
+    assert E == pytest.approx(Eo, rel=1e-4)
