@@ -64,6 +64,7 @@ struct gid_ctx {
     CUtensorMap r, t;
   };
   std::vector<Maps> maps;
+  CUtensorMap lin_map;      // the state X for the linearisation: box [V][BY + 6][BX + 8]
   bool map_failed = false;  // a tensor map could not be encoded (the launch was skipped)
   bool use_graph = true;
   std::vector<Graph> graphs;
@@ -204,27 +205,30 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// 3-D tensor map of V pitched planes at `base` with the given box (x, y, planes).
+static bool encode_planes(const gid_ctx* c, CUtensorMap* map, const float* base, cuuint32_t bx, cuuint32_t by,
+                          cuuint32_t bz) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->H, (cuuint64_t)c->V};
+  const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(float), (cuuint64_t)c->plane * sizeof(float)};
+  const cuuint32_t box[3] = {bx, by, bz};
+  const cuuint32_t es[3] = {1u, 1u, 1u};
+  return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 // Tensor maps of the V planes at `base` (pitched like every context plane) for
 // an operator tile of `th` rows; nullptr if the driver cannot encode them.
 static const gid_ctx::Maps* tile_maps(gid_ctx* c, const float* base, int th) {
   for (const auto& m : c->maps)
     if (m.base == base && m.th == th) return &m;
-  auto fn = encode_fn();
-  if (!fn) return nullptr;
   gid_ctx::Maps m;
   m.base = base;
   m.th = th;
-  const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->H, (cuuint64_t)c->V};
-  const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(float), (cuuint64_t)c->plane * sizeof(float)};
-  const cuuint32_t box_r[3] = {(cuuint32_t)VRW, (cuuint32_t)(th + 2 * AHR), 3u};
-  const cuuint32_t box_t[3] = {(cuuint32_t)VRW, (cuuint32_t)(th + 2), (cuuint32_t)(c->K + 1)};
-  const cuuint32_t es[3] = {1u, 1u, 1u};
-  auto enc = [&](CUtensorMap* map, const cuuint32_t* box) {
-    return fn(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, es,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-  };
-  if (!enc(&m.r, box_r) || !enc(&m.t, box_t)) return nullptr;
+  if (!encode_planes(c, &m.r, base, VRW, th + 2 * AHR, 3) || !encode_planes(c, &m.t, base, VRW, th + 2, c->K + 1))
+    return nullptr;
   c->maps.push_back(m);
   return &c->maps.back();
 }
@@ -234,7 +238,7 @@ static const gid_ctx::Maps* tile_maps(gid_ctx* c, const float* base, int th) {
 template <int K>
 struct Launch {
   static void linearize(const gid_ctx* c, int mode, float* g, float* dg) {
-    k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg);
+    k_linearize<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mode, g, dg, c->lin_map);
   }
   // k_apply and k_update are launched as programmatic dependents of the kernel
   // before them: each may start (prefetch, colour table) while that kernel
@@ -522,7 +526,7 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
     return fail(nullptr, GID_ERR_OOM, "internal pool layout");
   }
   GID_DISPATCH(c, prepare, c);
-  if (!tile_maps(c, c->z, c->apply_th)) {
+  if (!tile_maps(c, c->z, c->apply_th) || !encode_planes(c, &c->lin_map, c->X, LIN_C, LIN_R, c->V)) {
     cudaFree(c->pool);
     delete c;
     return fail(nullptr, GID_ERR_CUDA, "cuTensorMapEncodeTiled unavailable or failed for the operator tile");

@@ -25,6 +25,9 @@
 namespace gid {
 
 constexpr int BX = 32, BY = 8, NT = BX * BY;
+// X tile of the linearisation: BY + 6 rows, BX + 8 columns (pairs reach 3, rows
+// of 40 floats = 160 bytes keep every TMA row 16-byte aligned)
+constexpr int LIN_R = BY + 6, LIN_C = BX + 8;
 
 struct Weights {
   float ld, lcl, lrs, p, lrc, lm, lis, lsm, lnn, lIR, lCR, eps, sharp, tau;
@@ -258,6 +261,38 @@ struct CoefLayout {
 };
 constexpr int coef_planes(int K, int ns) { return 10 + 3 * (K + 1) + 2 * ns; }
 
+// ---- TMA: one elected thread copies a 3-D box of planes into shared memory,
+// completion counted in bytes on an mbarrier.
+constexpr long TMA_SPINS = 1L << 22;  // bounded wait (then ST_TIMEOUT)
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned done;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+// Box of the tensor map at (x, y, z) (x in elements, 16-byte aligned; may be
+// negative or past the end: those elements read as zero).
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(smem_addr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+      : "memory");
+}
+
 // ---------------------------------------------------------------- stencil helpers
 
 struct Pix {
@@ -474,25 +509,48 @@ __device__ __forceinline__ void load_state(const Params& P, const ColorTable<K>&
 // (writes g to gout and diag to dout); mode 2: coefficients only.
 template <int K>
 __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int mode, float* __restrict__ gout,
-                                                  float* __restrict__ dout) {
+                                                  float* __restrict__ dout,
+                                                  const __grid_constant__ CUtensorMap mapX) {
   constexpr int V = K + 4;
   __shared__ ColorTable<K> ct;
+  // the block's tile of X with the consistency pairs' reach: rows y0 - 3 ..
+  // y0 + BY + 2, columns x0 - 4 .. x0 + BX + 3 (one TMA box, zero outside)
+  __shared__ alignas(128) float sX[V][LIN_R][LIN_C];
+  __shared__ __align__(8) uint64_t bar;
   load_colors<K>(ct, P.col);
+  const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+  if (tid_flat() == 0) mbar_init(&bar, 1);
+  __syncthreads();
+  if (tid_flat() == 0) {
+    mbar_expect_tx(&bar, (unsigned)sizeof(sX));
+    tma_load_3d(&sX[0][0][0], &mapX, x0 - 4, y0 - 3, 0, &bar);
+  }
+  {
+    bool done = false;
+    for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
+    if (!done && tid_flat() == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+  }
+  // X reads go to the tile: the same indexing helpers with the tile's strides
+  // and a base that maps absolute (y, x) into it
+  Params Q = P;
+  Q.pitch = LIN_C;
+  Q.plane = (long)LIN_R * LIN_C;
+  Q.X = &sX[0][0][0] - ((long)(y0 - 3) * LIN_C + (x0 - 4));
   const Weights& w = P.w;
-  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   float rz = 0.f;
   if (x < P.W && y < P.H) {
     const Pix px = make_pix(P, x, y);
-    const long o = off2(P, y, x);
+    const long o = off2(P, y, x), oq = off2(Q, y, x);
     PixState<K> s;
-    load_state<K>(P, ct, o, s);
+    load_state<K>(Q, ct, oq, s);
     float g[V], dg[V];
 #pragma unroll
     for (int v = 0; v < V; v++) g[v] = dg[v] = 0.f;
     // Linear terms: g -= A_lin X and diag += diag(A_lin), with the same stencil
     // as normal_apply; the data term is handled separately below.
-    const float* X = P.X;
-    auto xf = [&](int v, int dy, int dx) { return X[v * P.plane + o + (long)dy * P.pitch + dx]; };
+    const float* X = Q.X;
+    auto xf = [&](int v, int dy, int dx) { return X[v * Q.plane + oq + (long)dy * Q.pitch + dx]; };
     // E_data: residual e_c = I_c - R_c S_c.
     for (int c = 0; c < 3; c++) {
       const float e = P.I[c * P.plane + o] - s.R[c] * s.S[c];
@@ -512,7 +570,7 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
       dg[c] += w.lcl;
     }
     // E_r-sparsity.
-    const Edges er = rsparse_edges(P, X, px);
+    const Edges er = rsparse_edges(Q, X, px);
     for (int c = 0; c < 3; c++) {
       g[c] -= edge_laplace(er, px, s.rr[c], [&](int dy, int dx) { return xf(c, dy, dx); });
       dg[c] += er.R + er.D + er.L + er.U;
@@ -577,7 +635,7 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
     // E_smoothness.
 #pragma unroll
     for (int k = 0; k <= K; k++) {
-      const Edges es = smooth_edges(P, X, 3 + k, px, s.T[k]);
+      const Edges es = smooth_edges(Q, X, 3 + k, px, s.T[k]);
       g[3 + k] -= edge_laplace(es, px, s.T[k], [&](int dy, int dx) { return xf(3 + k, dy, dx); });
       dg[3 + k] += es.R + es.D + es.L + es.U;
       cf[(CL::ER + k) * P.plane] = es.R;
@@ -703,38 +761,6 @@ struct ApplyShape<17> {
 // p = s (+ beta p_old) on the tile's pixels.  get_beta() is called once the
 // staging loads are in (it may wait on a block reduction).  Returns this
 // thread's share of <p, q>.  All threads of the block call it.
-// ---- TMA: one elected thread copies a 3-D box of planes into shared memory,
-// completion counted in bytes on an mbarrier.
-constexpr long TMA_SPINS = 1L << 22;  // bounded wait (then ST_TIMEOUT)
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
-__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-  asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
-  unsigned done;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(done)
-      : "r"(smem_addr(bar)), "r"(parity)
-      : "memory");
-  return done != 0;
-}
-// Box of the tensor map at (x, y, z) (x in elements, 16-byte aligned; may be
-// negative or past the end: those elements read as zero).
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
-      "[%5];\n" ::"r"(smem_addr(dst)),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
-      : "memory");
-}
-
 // 16-byte asynchronous global -> shared copy (L2 only); src_bytes = 0 writes
 // zeros and reads nothing.
 __device__ __forceinline__ void cp_async16(void* dst, const void* src, int src_bytes) {
