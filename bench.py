@@ -327,16 +327,16 @@ def run_gid(args, ws, rank, local):
     # end to end: the host-buffer entry point, host<->device copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        rgb_h = [torch.from_numpy(f.I.astype(np.float32)).pin_memory().numpy() for f in frames]
-        lab_h = [torch.from_numpy(f.labels.copy()).pin_memory().numpy() for f in frames]
-        R_h = torch.empty((3, H, W), dtype=torch.float32).pin_memory().numpy()
-        T_h = torch.empty((K + 1, H, W), dtype=torch.float32).pin_memory().numpy()
-        b_h = np.zeros((K, 3), np.float32)
+        # the whole video through the pipelined host-buffer entry point (page-locked buffers)
+        rgb_h = torch.from_numpy(np.stack([f.I.astype(np.float32) for f in frames])).pin_memory().numpy()
+        lab_h = torch.from_numpy(np.stack([f.labels for f in frames])).pin_memory().numpy()
+        R_h = torch.empty((F, 3, H, W), dtype=torch.float32).pin_memory().numpy()
+        T_h = torch.empty((F, K + 1, H, W), dtype=torch.float32).pin_memory().numpy()
+        b_h = torch.empty((F, K, 3), dtype=torch.float32).pin_memory().numpy()
 
         def e2e_step():
             s.new_sequence()
-            for t in range(F):
-                s.solve_frame_host(rgb_h[t], lab_h[t], 0 if t == 0 else 1, N, M, R_h, T_h, b_h)
+            s.solve_video_host(rgb_h, lab_h, 0, N, M, R_h, T_h, b_h)
 
         e2e_step()
         barrier(ws)

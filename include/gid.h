@@ -158,6 +158,18 @@ int gid_energy(gid_ctx* ctx, double* total, double* per_term);
 int gid_solve_frame_host(gid_ctx* ctx, const float* rgb_host, const uint8_t* labels_host, int init_mode,
                          int n_outer, int m_inner, float* R_host, float* T_host, float* b_host);
 
+/* A sequence of n frames with host buffers, pipelined: frame t + 1's upload and
+ * frame t's download run on a context-owned copy stream while frame t is
+ * solved (double-buffered device staging, ordered by events).  Per frame:
+ * gid_set_frame, gid_init (first_init_mode, 0 or 1, for frame 0; warm start
+ * for the others), gid_run(n_outer, m_inner), then R, T and the refined base
+ * colours of that frame.  rgb_host n x 3 x H x W, labels_host n x H x W,
+ * R_host n x 3 x H x W, T_host n x (K+1) x H x W, b_host n x K x 3 (outputs may
+ * be NULL).  Host buffers should be page-locked for the copies to overlap.
+ * Results equal n calls of gid_solve_frame_host.  Synchronises. */
+int gid_solve_video_host(gid_ctx* ctx, int n, const float* rgb_host, const uint8_t* labels_host,
+                         int first_init_mode, int n_outer, int m_inner, float* R_host, float* T_host, float* b_host);
+
 /* ---- single stages, for kernel-level checks (same kernels as gid_run) ---- */
 
 /* Per-frame precompute outputs: w_SR (H x W), spatial pair weights

@@ -42,6 +42,14 @@ struct gid_ctx {
   float* st_rgb = nullptr;
   uint8_t* st_lab = nullptr;
   float *st_R = nullptr, *st_T = nullptr;
+  // double-buffered staging and a copy stream for the pipelined video entry point
+  struct Pipe {
+    cudaStream_t cs = nullptr;
+    float *rgb[2] = {nullptr, nullptr}, *R[2] = {nullptr, nullptr}, *T[2] = {nullptr, nullptr},
+          *b[2] = {nullptr, nullptr};
+    uint8_t* lab[2] = {nullptr, nullptr};
+    cudaEvent_t up[2] = {}, ingested[2] = {}, solved[2] = {}, down[2] = {};
+  } pipe;
   bool has_colors = false, has_frame = false, initialised = false, temporal_active = false;
   int frames_solved = 0;
   long long launches = 0;  // kernels launched by this context
@@ -574,6 +582,21 @@ extern "C" void gid_destroy(gid_ctx* c) {
   cudaFree(c->st_lab);
   cudaFree(c->st_R);
   cudaFree(c->st_T);
+  if (c->pipe.cs) {
+    cudaStreamSynchronize(c->pipe.cs);
+    cudaStreamDestroy(c->pipe.cs);
+    for (int i = 0; i < 2; i++) {
+      cudaFree(c->pipe.rgb[i]);
+      cudaFree(c->pipe.lab[i]);
+      cudaFree(c->pipe.R[i]);
+      cudaFree(c->pipe.T[i]);
+      cudaFree(c->pipe.b[i]);
+      cudaEventDestroy(c->pipe.up[i]);
+      cudaEventDestroy(c->pipe.ingested[i]);
+      cudaEventDestroy(c->pipe.solved[i]);
+      cudaEventDestroy(c->pipe.down[i]);
+    }
+  }
   delete c;
 }
 
@@ -860,6 +883,66 @@ extern "C" int gid_solve_frame_host(gid_ctx* c, const float* rgb_host, const uin
                                       cudaMemcpyDeviceToHost, c->stream));
   }
   if (b_host) return gid_get_base_colors(c, b_host);
+  return sync_status(c);
+}
+
+extern "C" int gid_solve_video_host(gid_ctx* c, int n, const float* rgb_host, const uint8_t* labels_host,
+                                    int first_init_mode, int n_outer, int m_inner, float* R_host, float* T_host,
+                                    float* b_host) {
+  if (!c || !rgb_host || !labels_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (n < 1) return fail(c, GID_ERR_INVALID_ARG, "n >= 1 frames");
+  if (first_init_mode != 0 && first_init_mode != 1) return fail(c, GID_ERR_INVALID_ARG, "init mode 0 or 1");
+  const size_t HW = (size_t)c->H * c->W, rgb_b = 3 * HW * sizeof(float), R_b = 3 * HW * sizeof(float),
+               T_b = (size_t)(c->K + 1) * HW * sizeof(float), b_b = (size_t)c->K * 3 * sizeof(float);
+  auto& pp = c->pipe;
+  if (!pp.cs) {
+    GID_TRY_CUDA(c, cudaStreamCreateWithFlags(&pp.cs, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; i++) {
+      GID_TRY_CUDA(c, cudaMalloc(&pp.rgb[i], rgb_b));
+      GID_TRY_CUDA(c, cudaMalloc(&pp.lab[i], HW));
+      GID_TRY_CUDA(c, cudaMalloc(&pp.R[i], R_b));
+      GID_TRY_CUDA(c, cudaMalloc(&pp.T[i], T_b));
+      GID_TRY_CUDA(c, cudaMalloc(&pp.b[i], b_b));
+      for (cudaEvent_t* e : {&pp.up[i], &pp.ingested[i], &pp.solved[i], &pp.down[i]})
+        GID_TRY_CUDA(c, cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+    }
+  }
+  // slot i's staging is reused every other frame: an upload waits for the
+  // ingest of the frame two back, an output for the download of the frame two back
+  auto upload = [&](int t) -> int {
+    const int i = t & 1;
+    if (t >= 2) GID_TRY_CUDA(c, cudaStreamWaitEvent(pp.cs, pp.ingested[i], 0));
+    GID_TRY_CUDA(c, cudaMemcpyAsync(pp.rgb[i], rgb_host + (size_t)t * 3 * HW, rgb_b, cudaMemcpyHostToDevice, pp.cs));
+    GID_TRY_CUDA(c, cudaMemcpyAsync(pp.lab[i], labels_host + (size_t)t * HW, HW, cudaMemcpyHostToDevice, pp.cs));
+    GID_TRY_CUDA(c, cudaEventRecord(pp.up[i], pp.cs));
+    return GID_OK;
+  };
+  if (int rc = upload(0)) return rc;
+  const float* colors = reinterpret_cast<const float*>(reinterpret_cast<const char*>(c->col) + offsetof(DevColors, b));
+  for (int t = 0; t < n; t++) {
+    const int i = t & 1;
+    GID_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, pp.up[i], 0));
+    if (int rc = gid_set_frame(c, pp.rgb[i], pp.lab[i])) return rc;
+    GID_TRY_CUDA(c, cudaEventRecord(pp.ingested[i], c->stream));
+    if (t + 1 < n)
+      if (int rc = upload(t + 1)) return rc;  // overlaps this frame's solve
+    if (int rc = gid_init(c, t == 0 ? first_init_mode : 1)) return rc;
+    if (int rc = gid_run(c, n_outer, m_inner)) return rc;
+    if (t >= 2) GID_TRY_CUDA(c, cudaStreamWaitEvent(c->stream, pp.down[i], 0));
+    if (R_host || T_host)
+      if (int rc = gid_get_layers(c, pp.R[i], pp.T[i])) return rc;
+    GID_TRY_CUDA(c, cudaMemcpyAsync(pp.b[i], colors, b_b, cudaMemcpyDeviceToDevice, c->stream));
+    GID_TRY_CUDA(c, cudaEventRecord(pp.solved[i], c->stream));
+    // download frame t on the copy stream while frame t + 1 is solved
+    GID_TRY_CUDA(c, cudaStreamWaitEvent(pp.cs, pp.solved[i], 0));
+    if (R_host) GID_TRY_CUDA(c, cudaMemcpyAsync(R_host + (size_t)t * 3 * HW, pp.R[i], R_b, cudaMemcpyDeviceToHost, pp.cs));
+    if (T_host)
+      GID_TRY_CUDA(c, cudaMemcpyAsync(T_host + (size_t)t * (c->K + 1) * HW, pp.T[i], T_b, cudaMemcpyDeviceToHost,
+                                      pp.cs));
+    if (b_host) GID_TRY_CUDA(c, cudaMemcpyAsync(b_host + (size_t)t * c->K * 3, pp.b[i], b_b, cudaMemcpyDeviceToHost, pp.cs));
+    GID_TRY_CUDA(c, cudaEventRecord(pp.down[i], pp.cs));
+  }
+  GID_TRY_CUDA(c, cudaStreamSynchronize(pp.cs));
   return sync_status(c);
 }
 

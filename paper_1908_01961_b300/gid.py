@@ -35,6 +35,7 @@ EXPORTS = (
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
     "gid_net_set_weights", "gid_net_get_weights", "gid_net_get_grads", "gid_net_forward", "gid_net_backward",
     "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned", "gid_base_color_step",
+    "gid_solve_video_host",
 )
 
 
@@ -131,6 +132,7 @@ def load():
     L.gid_net_set_loss_weights.argtypes = [P, ctypes.c_float, ctypes.c_float, ctypes.c_float]
     L.gid_init_learned.argtypes = [P, P, ctypes.c_float]
     L.gid_base_color_step.argtypes = [P]
+    L.gid_solve_video_host.argtypes = [P, I, P, P, I, I, I, P, P, P]
     for n in EXPORTS:
         if n not in ("gid_default_weights", "gid_destroy", "gid_last_error", "gid_batch_destroy",
                      "gid_batch_last_error", "gid_batch_ctx", "gid_net_destroy", "gid_net_last_error",
@@ -287,6 +289,15 @@ class Solver:
             return None if a is None else ctypes.c_void_p(a.ctypes.data)
         self._chk(self.lib.gid_solve_frame_host(self.h, p(rgb), p(labels), init_mode, n_outer, m_inner,
                                                 p(R), p(T), p(b)))
+
+    def solve_video_host(self, rgb, labels, first_init_mode, n_outer, m_inner, R=None, T=None, b=None):
+        """Pipelined host-buffer entry point for a sequence (gid_solve_video_host);
+        rgb (n, 3, H, W), labels (n, H, W) and the optional outputs are numpy
+        arrays (ideally page-locked)."""
+        def p(a):
+            return None if a is None else ctypes.c_void_p(a.ctypes.data)
+        self._chk(self.lib.gid_solve_video_host(self.h, rgb.shape[0], p(rgb), p(labels), first_init_mode, n_outer,
+                                                m_inner, p(R), p(T), p(b)))
 
     # -- stages
     def stage_precompute(self):

@@ -288,3 +288,22 @@ def test_end_to_end_edge_shapes(H, W, K, n_cells):
     assert np.abs(T - To).max() <= 1e-3
     assert np.abs(b - bo).max() <= 1e-3
     assert E == pytest.approx(Eo, rel=1e-4)
+
+
+def test_pipelined_video_host_entry_matches_frame_by_frame():
+    """gid_solve_video_host (uploads and downloads overlapped with the solves)
+    gives, frame for frame, the bits of consecutive gid_solve_frame_host calls."""
+    case = Case(H=48, W=64, K=4, n_cells=12, seed=8, frames=4, temporal=True)
+    F, H, W, K = 4, case.H, case.W, case.K
+    rgb = np.ascontiguousarray(np.stack([f.I for f in case.frames]), np.float32)
+    lab = np.ascontiguousarray(np.stack([f.labels for f in case.frames]), np.uint8)
+    s1 = case.solver()
+    R1 = np.zeros((F, 3, H, W), np.float32)
+    T1 = np.zeros((F, K + 1, H, W), np.float32)
+    b1 = np.zeros((F, K, 3), np.float32)
+    for t in range(F):
+        s1.solve_frame_host(rgb[t], lab[t], 0 if t == 0 else 1, 2, 6, R1[t], T1[t], b1[t])
+    s2 = case.solver()
+    R2, T2, b2 = np.zeros_like(R1), np.zeros_like(T1), np.zeros_like(b1)
+    s2.solve_video_host(rgb, lab, 0, 2, 6, R2, T2, b2)
+    assert np.array_equal(R1, R2) and np.array_equal(T1, T2) and np.array_equal(b1, b2)
