@@ -348,6 +348,43 @@ def run_gid(args, ws, rank, local):
                "h2d_bytes_per_step": F * (3 * P * 4 + P),
                "d2h_bytes_per_step": F * ((3 + K + 1) * P * 4 + K * 3 * 4)}
 
+    # editing (Sec. 7.4): recombination of the last frame's layers with one recoloured
+    # object, one re-keyed and one suppressed indirect layer
+    editing = None
+    if rank == 0:
+        bn = s.base_colors().copy()
+        bn[0] = bn[0][::-1]
+        gains = np.ones(K, np.float32)
+        gains[1] = 0.0
+        mask = (lab[F - 1] == 2).to(torch.uint8) * 3
+        out = torch.empty((3, H, W), device=dev)
+        for _ in range(3):
+            s.recombine(bn, gains, mask, out)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 50
+        e0.record(stream)
+        for _ in range(reps):
+            s.recombine(bn, gains, mask, out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        us = 1000.0 * e0.elapsed_time(e1) / reps
+        eb = 4.0 * P * (K + 4) + P + 4.0 * 3 * P   # read X and the mask, write the image
+        editing = {"kernel": "k_recombine", "us_per_frame": us, "algorithmic_bytes": eb,
+                   "achieved_GBps": eb / (us * 1e-6) / 1e9, "note": "host call included (gains and colours "
+                   "passed by value)"}
+
+    # chromaticity clustering of frame 0 (Sec. 4.1), the step before the solve
+    clustering = None
+    if rank == 0:
+        for _ in range(3):
+            gid.cluster(rgb[0])
+        t0 = time.perf_counter()
+        reps = 20
+        for _ in range(reps):
+            labs, bcl = gid.cluster(rgb[0])
+        clustering = {"ms_per_frame": 1000.0 * (time.perf_counter() - t0) / reps, "clusters": int(bcl.shape[0]),
+                      "note": "host wall time of gid_cluster (4 kernels, scratch allocation, synchronising)"}
+
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_arm(dev, flush)
@@ -371,7 +408,7 @@ def run_gid(args, ws, rank, local):
                           (f" (autotuned; us per PCG step {tile_us})" if args.tile is None else " (fixed)")},
                "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
                "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E,
-               "learned_warm_start": learned}
+               "learned_warm_start": learned, "editing": editing, "clustering": clustering}
         print(json.dumps(out), flush=True)
 
 

@@ -131,6 +131,20 @@ int gid_set_graphs(gid_ctx* ctx, int enable);
  * = T_0..T_K.  Either pointer may be NULL.  Asynchronous. */
 int gid_get_layers(gid_ctx* ctx, float* R_dev, float* T_dev);
 
+/* Layer recombination for the editing applications of Sec. 7.4, from the
+ * current layers and refined base colours b:
+ *     out(x) = R'(x) * (T_0(x) + sum_k g_k b'_k T_k(x)),
+ *     R'_c(x) = R_c(x) * b'_jc / b_jc where mask(x) = j in 1..K and b_jc != 0,
+ *               else R_c(x).
+ * Recolouring an object: a new colour b'_j and a mask of its pixels (its
+ * indirect light on other surfaces follows b'_j); colour keying: a new colour
+ * for one indirect layer, no mask; spill suppression: gain g_k = 0 for the
+ * spilling layer.  b_new_host K x 3 (finite; NULL = b), gain_host K
+ * (NULL = all 1), mask_dev H x W uint8 (NULL = none; values > K count as 0),
+ * out_dev 3 x H x W float32, device.  Async unless b_new_host is NULL. */
+int gid_recombine(gid_ctx* ctx, const float* b_new_host, const float* gain_host, const uint8_t* mask_dev,
+                  float* out_dev);
+
 /* Raw unknowns X ((K+4) x H x W: r_R, r_G, r_B, T_0..T_K, r = ln R) to / from
  * device memory.  gid_set_state also marks the context initialised.  Async. */
 int gid_get_state(gid_ctx* ctx, float* X_dev);
@@ -169,6 +183,27 @@ int gid_solve_frame_host(gid_ctx* ctx, const float* rgb_host, const uint8_t* lab
  * Results equal n calls of gid_solve_frame_host.  Synchronises. */
 int gid_solve_video_host(gid_ctx* ctx, int n, const float* rgb_host, const uint8_t* labels_host,
                          int first_init_mode, int n_outer, int m_inner, float* R_host, float* T_host, float* b_host);
+
+/* Chromaticity clustering of Sec. 4.1, on the GPU: the initial base colours
+ * and the cluster labels a solve starts from.  Chromaticity C = I /
+ * (I_R + I_G + I_B + 1e-6); a histogram with 10 partitions per axis of C in
+ * [0, 1]^3 (outside values in the edge bins); weighted k-means on the occupied
+ * bins' mid-points weighted by their populations, at most k_max centres
+ * initialised at the k_max most populated bins (ties by bin index), iterated
+ * until no bin changes cluster (at most 100 times); while two centres are
+ * closer than merge_dist (the paper's 0.2) the smaller cluster joins the
+ * larger (population-weighted centre, closest pair first); clusters ordered by
+ * decreasing population; every pixel labelled with its closest centre; initial
+ * base colours = the mean RGB of each cluster's pixels.
+ *   rgb_dev     3 x H x W float32 frame (device)
+ *   k_max       1..GID_MAX_K (the paper uses 10)
+ *   labels_dev  out, H x W uint8 in 0..k_out-1 (device)
+ *   b_host      out, k_out x 3 float32 (room for k_max x 3)
+ *   k_out       out, the number of clusters after merging
+ * Allocates and frees its own scratch; synchronises the stream.  Errors are
+ * written to errbuf (may be NULL). */
+int gid_cluster(int H, int W, const float* rgb_dev, int k_max, float merge_dist, void* stream, uint8_t* labels_dev,
+                float* b_host, int* k_out, char* errbuf, int errbuf_len);
 
 /* ---- single stages, for kernel-level checks (same kernels as gid_run) ---- */
 

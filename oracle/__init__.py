@@ -253,6 +253,107 @@ def fit_direct(I, X, b):
     return X
 
 
+def recombine(X, b, b_new, gains, mask):
+    """Layer recombination of Sec. 7.4 (recolouring, colour keying, spill
+    suppression): out = R' * (T_0 + sum_k g_k b'_k T_k) with R'_c = R_c b'_jc /
+    b_jc on the pixels whose mask is j in 1..K where b_jc != 0 (other pixels
+    keep R).
+    X (K+4, H, W), b and b_new (K, 3), gains (K,), mask (H, W) ints."""
+    X = _f64(X)
+    b, b_new, gains = _f64(b).reshape(-1, 3), _f64(b_new).reshape(-1, 3), _f64(gains).ravel()
+    K = b.shape[0]
+    R = np.exp(X[:3])
+    S = X[3][None] + np.einsum("k,kc,khw->chw", gains, b_new, X[4:])
+    ratio = np.ones((K + 1, 3))
+    ratio[1:] = np.where(b != 0.0, b_new / np.where(b != 0.0, b, 1.0), 1.0)
+    m = np.where(np.asarray(mask) <= K, np.asarray(mask), 0)
+    return R * ratio[m].transpose(2, 0, 1) * S
+
+
+def chromaticity32(I):
+    """C = I / (I_R + I_G + I_B + 1e-6) in float32, in that order of operations
+    (the precision and order the CUDA ingest uses, so that bin and cluster
+    decisions are taken on identical values)."""
+    I = np.asarray(I, np.float32)
+    s = (I[0] + I[1]) + I[2] + np.float32(1e-6)
+    return I / s[None]
+
+
+CLUSTER_BINS = 10
+
+
+def cluster(I, k_max, merge_dist=0.2, max_iter=100):
+    """Chromaticity clustering of Sec. 4.1, steps in the paper's order:
+    1. chromaticity C of every pixel;
+    2. histogram with 10 partitions per axis of (C_R, C_G, C_B) in [0, 1]
+       (values outside, from negative noisy channels, count in the edge bins);
+    3. weighted k-means with the bins' mid-points as samples and their
+       populations as weights, at most k_max clusters (initial centres: the
+       k_max most populated bins, ties by bin index; iterate until no bin
+       changes cluster, at most max_iter times);
+    4. merging: while two centres are closer than merge_dist (Euclidean
+       chromaticity distance), the smaller cluster (by population) joins the
+       larger, whose centre becomes the population-weighted mean of both
+       (closest pair first; empty clusters are dropped);
+    5. every pixel is assigned to its closest centre (its own chromaticity,
+       distances in float64);
+    6. initial base colours: the mean RGB of each cluster's pixels.
+    Clusters are ordered by decreasing population (ties by centre order).
+    Returns (labels (H, W) uint8, b_init (K', 3) float64, centres (K', 3))."""
+    I = np.asarray(I)
+    C = chromaticity32(I)
+    nb = CLUSTER_BINS
+    idx = np.clip((C * np.float32(nb)).astype(np.int32), 0, nb - 1)          # (3, H, W); outside [0, 1] -> edge bins
+    flat = (idx[0] * nb + idx[1]) * nb + idx[2]
+    hist = np.bincount(flat.ravel(), minlength=nb ** 3).astype(np.float64)
+    mids = (np.stack(np.meshgrid(np.arange(nb), np.arange(nb), np.arange(nb), indexing="ij"), -1).reshape(-1, 3)
+            + 0.5) / nb
+    occ = np.nonzero(hist)[0]
+    w, x = hist[occ], mids[occ]
+    order = sorted(range(len(occ)), key=lambda i: (-w[i], occ[i]))
+    k = min(k_max, len(occ))
+    centres = x[order[:k]].copy()
+    assign = np.full(len(occ), -1)
+    for _ in range(max_iter):
+        d = ((x[:, None, :] - centres[None, :, :]) ** 2).sum(-1)
+        new = d.argmin(axis=1)
+        if np.array_equal(new, assign):
+            break
+        assign = new
+        for j in range(k):
+            sel = assign == j
+            if w[sel].sum() > 0:
+                centres[j] = (w[sel][:, None] * x[sel]).sum(0) / w[sel].sum()
+    pop = np.array([w[assign == j].sum() for j in range(k)])
+    alive = [j for j in range(k) if pop[j] > 0]
+    cen = {j: centres[j].copy() for j in alive}
+    pw = {j: pop[j] for j in alive}
+    while len(alive) > 1:
+        best = None
+        for a in range(len(alive)):
+            for b in range(a + 1, len(alive)):
+                ja, jb = alive[a], alive[b]
+                dist = np.sqrt(((cen[ja] - cen[jb]) ** 2).sum())
+                if dist < merge_dist and (best is None or dist < best[0]):
+                    best = (dist, ja, jb)
+        if best is None:
+            break
+        _, ja, jb = best
+        big, small = (ja, jb) if (pw[ja], -ja) >= (pw[jb], -jb) else (jb, ja)
+        cen[big] = (pw[big] * cen[big] + pw[small] * cen[small]) / (pw[big] + pw[small])
+        pw[big] += pw[small]
+        alive.remove(small)
+    alive.sort(key=lambda j: (-pw[j], j))
+    centres = np.array([cen[j] for j in alive])
+    Cd = C.astype(np.float64)
+    d = ((Cd[None] - centres[:, :, None, None]) ** 2).sum(1)                  # (K', H, W)
+    labels = d.argmin(axis=0).astype(np.uint8)
+    I64 = I.astype(np.float64)
+    b = np.array([I64[:, labels == j].mean(axis=1) if np.any(labels == j) else centres[j]
+                  for j in range(len(alive))])
+    return labels, b, centres
+
+
 def dense_solve(A, g):
     """Delta b (K, 3) from the three K x K blocks by SVD pseudo-inverse (Sec. 6.1)."""
     K = A.shape[1]

@@ -13,7 +13,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgid.so")
-SOURCES = ["gid.cu", "gid_noalloc.cu", "gid_net.cu"]
+SOURCES = ["gid.cu", "gid_noalloc.cu", "gid_net.cu", "gid_cluster.cu"]
 HEADERS = ["gid_kernels.cuh", "gid_net_kernels.cuh", "gid_net_internal.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -350,6 +350,9 @@ struct Launch {
   static void energy(const gid_ctx* c) { k_energy<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void init_cold(const gid_ctx* c) { k_init_cold<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void fit_direct(const gid_ctx* c) { k_fit_direct<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
+  static void recombine(const gid_ctx* c, const EditTable& e, const uint8_t* mask, float* out) {
+    k_recombine<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), e, mask, out);
+  }
   static void readout(const gid_ctx* c, float* R, float* T) {
     k_readout<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), R, T);
   }
@@ -825,6 +828,31 @@ extern "C" int gid_get_layers(gid_ctx* c, float* R_dev, float* T_dev) {
   if (!R_dev && !T_dev) return GID_OK;
   launch(c, GID_KIND_READOUT, [&] { GID_DISPATCH(c, readout, c, R_dev, T_dev); });
   return check_launch(c, "k_readout");
+}
+
+extern "C" int gid_recombine(gid_ctx* c, const float* b_new_host, const float* gain_host, const uint8_t* mask_dev,
+                             float* out_dev) {
+  if (!c || !out_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
+  if (!c->initialised || !c->has_colors) return fail(c, GID_ERR_STATE, "no state / base colours");
+  EditTable e;
+  if (b_new_host) {
+    for (int i = 0; i < 3 * c->K; i++) {
+      if (!std::isfinite(b_new_host[i])) return fail(c, GID_ERR_INVALID_ARG, "new base colours must be finite");
+      e.bn[i] = b_new_host[i];
+    }
+  } else {
+    DevColors h;
+    GID_TRY_CUDA(c, cudaMemcpyAsync(&h, c->col, sizeof(h), cudaMemcpyDeviceToHost, c->stream));
+    GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+    for (int i = 0; i < 3 * c->K; i++) e.bn[i] = h.b[i];
+  }
+  for (int k = 0; k < c->K; k++) {
+    const float g = gain_host ? gain_host[k] : 1.f;
+    if (!std::isfinite(g)) return fail(c, GID_ERR_INVALID_ARG, "layer gains must be finite");
+    e.gain[k] = g;
+  }
+  launch(c, GID_KIND_READOUT, [&] { GID_DISPATCH(c, recombine, c, e, mask_dev, out_dev); });
+  return check_launch(c, "k_recombine");
 }
 
 extern "C" int gid_get_state(gid_ctx* c, float* X_dev) {

@@ -1443,4 +1443,39 @@ __global__ void k_readout(Params P, float* __restrict__ Rout, float* __restrict_
     for (int k = 0; k <= K; k++) Tout[k * HW + dst] = P.X[(3 + k) * P.plane + o];
 }
 
+// ---------------------------------------------------------------- editing
+
+// New base colours and per-layer gains of a layer recombination.
+struct EditTable {
+  float bn[GID_MAX_K * 3];
+  float gain[GID_MAX_K];
+};
+
+// Layer recombination (Sec. 7.4): I'(x) = R'(x) (T_0 + sum_k g_k b'_k T_k(x)),
+// R'_c = R_c b'_jc / b_jc where mask(x) = j in 1..K (the pixel belongs to an
+// object of base colour j being recoloured) and b_jc != 0, else R.  b is the
+// context's current (refined) colour set.  Planar output, 3 x H x W.
+template <int K>
+__global__ void k_recombine(Params P, EditTable e, const uint8_t* __restrict__ mask, float* __restrict__ out) {
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  if (x >= P.W || y >= P.H) return;
+  const long o = off2(P, y, x), HW = (long)P.H * P.W, dst = (long)y * P.W + x;
+  float T[K + 1];
+#pragma unroll
+  for (int k = 0; k <= K; k++) T[k] = P.X[(3 + k) * P.plane + o];
+  int j = mask ? mask[dst] : 0;
+  j = j <= K ? j : 0;
+  for (int c = 0; c < 3; c++) {
+    float S = T[0];
+#pragma unroll
+    for (int k = 1; k <= K; k++) S += e.gain[k - 1] * e.bn[(k - 1) * 3 + c] * T[k];
+    float R = expf(P.X[c * P.plane + o]);
+    if (j > 0) {
+      const float bo = P.col->b[(j - 1) * 3 + c];
+      if (bo != 0.f) R *= e.bn[(j - 1) * 3 + c] / bo;
+    }
+    out[c * HW + dst] = R * S;
+  }
+}
+
 }  // namespace gid

@@ -35,7 +35,7 @@ EXPORTS = (
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
     "gid_net_set_weights", "gid_net_get_weights", "gid_net_get_grads", "gid_net_forward", "gid_net_backward",
     "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned", "gid_base_color_step",
-    "gid_solve_video_host",
+    "gid_solve_video_host", "gid_recombine", "gid_cluster",
 )
 
 
@@ -133,6 +133,8 @@ def load():
     L.gid_init_learned.argtypes = [P, P, ctypes.c_float]
     L.gid_base_color_step.argtypes = [P]
     L.gid_solve_video_host.argtypes = [P, I, P, P, I, I, I, P, P, P]
+    L.gid_recombine.argtypes = [P, F, F, P, P]
+    L.gid_cluster.argtypes = [I, I, P, I, ctypes.c_float, P, P, F, ctypes.POINTER(I), ctypes.c_char_p, I]
     for n in EXPORTS:
         if n not in ("gid_default_weights", "gid_destroy", "gid_last_error", "gid_batch_destroy",
                      "gid_batch_last_error", "gid_batch_ctx", "gid_net_destroy", "gid_net_last_error",
@@ -178,6 +180,24 @@ def dense_refine_noalloc(X, rgb, b_init, weights=None, A=None, g=None, b=None, s
     if rc != GID_OK:
         raise GidError(rc, err.value.decode())
     return A, g, b
+
+
+def cluster(rgb, k_max=10, merge_dist=0.2, labels=None, stream=None):
+    """Chromaticity clustering of a (3, H, W) float32 CUDA frame (gid_cluster).
+    Returns (labels (H, W) uint8 CUDA tensor, b_init (K', 3) numpy float32)."""
+    import torch
+    _, H, W = rgb.shape
+    assert rgb.is_cuda and rgb.is_contiguous() and rgb.dtype == torch.float32
+    labels = torch.empty((H, W), dtype=torch.uint8, device=rgb.device) if labels is None else labels
+    b = np.zeros((MAX_K, 3), np.float32)
+    k = ctypes.c_int()
+    err = ctypes.create_string_buffer(256)
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    rc = load().gid_cluster(H, W, _ptr(rgb), k_max, merge_dist, ctypes.c_void_p(s), _ptr(labels),
+                            b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(k), err, 256)
+    if rc != GID_OK:
+        raise GidError(rc, err.value.decode())
+    return labels, b[:k.value].copy()
 
 
 def _ptr(t):
@@ -263,6 +283,20 @@ class Solver:
         T = self._dev((self.K + 1, self.H, self.W)) if T is None else T
         self._chk(self.lib.gid_get_layers(self.h, _ptr(R), _ptr(T)))
         return R, T
+
+    def recombine(self, b_new=None, gains=None, mask=None, out=None):
+        """Edited image from the current layers (gid_recombine): new base colours
+        (K, 3), per-layer gains (K,), a uint8 CUDA mask (H, W) of recoloured
+        objects (j = colour index + 1).  Returns a (3, H, W) CUDA tensor."""
+        F = ctypes.POINTER(ctypes.c_float)
+        bn = None if b_new is None else np.ascontiguousarray(b_new, np.float32).reshape(self.K, 3)
+        g = None if gains is None else np.ascontiguousarray(gains, np.float32).reshape(self.K)
+        if mask is not None:
+            self._check_dev(mask, (self.H, self.W), self.torch.uint8)
+        out = self._dev((3, self.H, self.W)) if out is None else out
+        self._chk(self.lib.gid_recombine(self.h, None if bn is None else bn.ctypes.data_as(F),
+                                         None if g is None else g.ctypes.data_as(F), _ptr(mask), _ptr(out)))
+        return out
 
     def state(self):
         X = self._dev((self.V, self.H, self.W))

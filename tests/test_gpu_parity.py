@@ -307,3 +307,28 @@ def test_pipelined_video_host_entry_matches_frame_by_frame():
     R2, T2, b2 = np.zeros_like(R1), np.zeros_like(T1), np.zeros_like(b1)
     s2.solve_video_host(rgb, lab, 0, 2, 6, R2, T2, b2)
     assert np.array_equal(R1, R2) and np.array_equal(T1, T2) and np.array_equal(b1, b2)
+
+
+def test_recombine_matches_oracle():
+    """gid_recombine (Sec. 7.4 editing) on a solved state against the oracle's
+    recombination with the GPU's own layers and refined colours: new colours,
+    mixed gains (a suppressed layer, an amplified one), a recoloured object and
+    out-of-range mask values (treated as 0)."""
+    case = Case(**CASES["70x41_K6"], seed=4)
+    s = case.solver()
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    s.init(0)
+    s.run(2, 6)
+    X = s.state().cpu().numpy().astype(np.float64)
+    b = s.base_colors().astype(np.float64)
+    rng = np.random.default_rng(3)
+    bn = (b * rng.uniform(0.5, 1.5, b.shape)).astype(np.float32)
+    g = np.array([1.0, 0.0, 1.0, 0.5, 2.0, 1.0], np.float32)
+    mask = np.where(case.frames[0].labels == 2, 3, 0).astype(np.uint8)
+    mask[0, :5] = 200
+    out = s.recombine(bn, g, torch.from_numpy(mask).cuda())
+    ref = O.recombine(X, b, bn.astype(np.float64), g.astype(np.float64), mask)
+    close(out.cpu().numpy(), ref, 1e-5, "recombined image")
+    same = s.recombine()                                  # b and unit gains: the model's reconstruction
+    close(same.cpu().numpy(), O.recombine(X, b, b, np.ones(6), np.zeros_like(mask)), 1e-5, "reconstruction")

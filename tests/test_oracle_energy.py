@@ -197,3 +197,85 @@ def test_fit_direct_recovers_ground_truth_and_minimises_the_data_term():
     Xn = Xw.copy()
     Xn[4:] = 5.0                                            # indirect light far above the image
     assert np.all(O.fit_direct(f.I, Xn, f.b)[3] == 0.0)
+
+
+def test_recombine_pins():
+    """Sec. 7.4 recombination: unchanged colours and gains reproduce the
+    image-formation model (the noise-free frame); zero gains leave direct light
+    only; recolouring an object by a factor scales exactly its pixels; a new
+    colour for one indirect layer changes only pixels that layer reaches."""
+    v = synth.SyntheticVideo(24, 32, 4, 6, seed=9, noise=0.0)
+    f = v.frame(0, noise=False)
+    X = np.concatenate([np.log(f.R), f.T])
+    K, ones = 4, np.ones(4)
+    mask0 = np.zeros((24, 32), int)
+    assert np.allclose(O.recombine(X, f.b, f.b, ones, mask0), f.I, rtol=1e-13, atol=1e-15)
+    assert np.allclose(O.recombine(X, f.b, f.b, np.zeros(K), mask0), f.R * f.T[0], rtol=1e-13)
+    j = 2
+    mask = np.where(f.labels == j - 1, j, 0)
+    bn = f.b.copy()
+    bn[j - 1] *= 1.5
+    out = O.recombine(X, f.b, bn, ones, mask)
+    base = O.recombine(X, f.b, bn, ones, mask0)
+    sel = f.labels == j - 1
+    assert np.allclose(out[:, sel], 1.5 * base[:, sel], rtol=1e-13)
+    assert np.allclose(out[:, ~sel], base[:, ~sel], rtol=1e-13)
+    bk = f.b.copy()
+    bk[0] = [0.9, 0.1, 0.1]
+    key = O.recombine(X, f.b, bk, ones, mask0)
+    untouched = f.T[1] == 0
+    assert np.allclose(key[:, untouched], f.I[:, untouched], rtol=1e-13, atol=1e-15)
+    assert not np.allclose(key[:, ~untouched], f.I[:, ~untouched])
+
+
+def _blocks(colors, H=20, W=30):
+    """An image of vertical stripes, one per colour."""
+    I = np.zeros((3, H, W))
+    n = len(colors)
+    for i, c in enumerate(colors):
+        I[:, :, i * W // n:(i + 1) * W // n] = np.asarray(c)[:, None, None]
+    return I
+
+
+def test_cluster_uniform_and_separated_colours():
+    """One colour -> one cluster of that colour; colours whose chromaticities are
+    far apart (> 0.2) -> one cluster each, the stripes as labels and the exact
+    colours as initial base colours (Sec. 4.1)."""
+    lab, b, _ = O.cluster(_blocks([(0.3, 0.5, 0.2)]), 10)
+    assert b.shape == (1, 3) and np.all(lab == 0) and np.allclose(b[0], [0.3, 0.5, 0.2])
+    cols = [(0.8, 0.1, 0.1), (0.1, 0.8, 0.1), (0.1, 0.1, 0.8)]
+    I = _blocks(cols)
+    lab, b, _ = O.cluster(I, 10)
+    assert b.shape == (3, 3)
+    for i, c in enumerate(cols):
+        stripe = lab[:, i * 10:(i + 1) * 10]
+        assert np.all(stripe == stripe[0, 0])
+        assert np.allclose(b[stripe[0, 0]], c)
+    assert len(set(lab[0, ::10])) == 3
+
+
+def test_cluster_merges_close_chromaticities_and_respects_k_max():
+    """Two colours 0.05 apart in chromaticity merge into the larger cluster (the
+    0.2 threshold); with k_max = 2, four well separated colours give at most two
+    clusters; brightness alone (same chromaticity) never separates pixels."""
+    I = _blocks([(0.6, 0.3, 0.1), (0.55, 0.33, 0.12), (0.6, 0.3, 0.1)])
+    lab, b, _ = O.cluster(I, 10)
+    assert b.shape[0] == 1 and np.all(lab == 0)
+    I = _blocks([(0.8, 0.1, 0.1), (0.1, 0.8, 0.1), (0.1, 0.1, 0.8), (0.45, 0.45, 0.1)], W=40)
+    lab, b, _ = O.cluster(I, 2)
+    assert 1 <= b.shape[0] <= 2
+    I = _blocks([(0.2, 0.4, 0.1), (0.4, 0.8, 0.2)])             # same chromaticity, twice as bright
+    lab, b, _ = O.cluster(I, 10)
+    assert b.shape[0] == 1 and np.allclose(b[0], [0.3, 0.6, 0.15])
+
+
+def test_cluster_weighted_kmeans_centre_is_population_weighted():
+    """Bins of one cluster: the centre is the population-weighted mean of their
+    mid-points (two bins 0.1 apart, populations 3:1)."""
+    H, W = 4, 4
+    I = np.zeros((3, H, W))
+    I[:, :, :3] = np.array([0.62, 0.33, 0.05])[:, None, None]     # bin (6, 3, 0)
+    I[:, :, 3:] = np.array([0.55, 0.42, 0.03])[:, None, None]     # bin (5, 4, 0)
+    lab, b, cen = O.cluster(I, 10)
+    assert cen.shape == (1, 3)
+    assert np.allclose(cen[0], (3 * np.array([0.65, 0.35, 0.05]) + np.array([0.55, 0.45, 0.05])) / 4)
