@@ -385,6 +385,18 @@ def run_gid(args, ws, rank, local):
         clustering = {"ms_per_frame": 1000.0 * (time.perf_counter() - t0) / reps, "clusters": int(bcl.shape[0]),
                       "note": "host wall time of gid_cluster (4 kernels, scratch allocation, synchronising)"}
 
+    # misclustering correction (Sec. 4.2) of one region of frame 0: K candidate solves as one batch
+    correction = None
+    if rank == 0:
+        region = torch.zeros((H, W), dtype=torch.uint8, device=dev)
+        region[H // 4:H // 2, W // 4:W // 2] = (lab[0][H // 4:H // 2, W // 4:W // 2] == int(lab[0][H // 3, W // 3]))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        best, sp, _ = gid.correct_region(rgb[0], lab[0], b0, region, w, N, M)
+        correction = {"ms": 1000.0 * (time.perf_counter() - t0), "candidates": K, "region_pixels":
+                      int(region.sum().item()), "winner": best, "note": "host wall time: K contexts created, "
+                      "solved as one batch (8 GN x 20 PCG each), region energies, destroyed"}
+
     learned = None
     if rank == 0 and not args.no_learned:
         learned = learned_arm(dev, flush)
@@ -408,7 +420,8 @@ def run_gid(args, ws, rank, local):
                           (f" (autotuned; us per PCG step {tile_us})" if args.tile is None else " (fixed)")},
                "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
                "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E,
-               "learned_warm_start": learned, "editing": editing, "clustering": clustering}
+               "learned_warm_start": learned, "editing": editing, "clustering": clustering,
+               "misclustering_correction": correction}
         print(json.dumps(out), flush=True)
 
 

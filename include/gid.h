@@ -164,6 +164,13 @@ int gid_base_color_step(gid_ctx* ctx);
  * error a device step recorded since the last synchronising call. */
 int gid_energy(gid_ctx* ctx, double* total, double* per_term);
 
+/* gid_energy restricted to the pixels where mask_dev (H x W uint8, device) is
+ * nonzero: each pixel contributes its data, clustering, monochrome, i-sparsity
+ * and non-neg terms and the r-sparsity, smoothness and consistency terms
+ * evaluated at it (so complementary masks add up to gid_energy).  NULL = all
+ * pixels.  Synchronises. */
+int gid_energy_region(gid_ctx* ctx, const uint8_t* mask_dev, double* total, double* per_term);
+
 /* One whole frame with host buffers: copy rgb_host (3 x H x W) and labels_host
  * (H x W) to the device, gid_set_frame, gid_init(init_mode), gid_run(n_outer,
  * m_inner), copy R (3 x H x W), T ((K+1) x H x W) and the refined base colours
@@ -360,6 +367,28 @@ int gid_net_adam_step(gid_net* net, float lr, float beta1, float beta2, float ep
  * layers.  Needs gid_set_base_colors and gid_set_frame, the same K, and H, W
  * multiples of 8.  Runs on the context stream.  Async. */
 int gid_init_learned(gid_ctx* ctx, gid_net* net, float zero_below);
+
+/* ---- misclustering correction (Sec. 4.2) ---- */
+
+/* Reflectance correction of a misclustered region: for every candidate base
+ * colour k = 1..K, a full decomposition of the frame (cold start, n_outer x
+ * m_inner, refinement per the weights) with the region's pixels labelled k;
+ * the K candidates are solved together as one batch (one graph launch per
+ * outer step).  Each candidate's i-sparsity energy (eq:shading-sparsity-term)
+ * over the region is measured and the sparsest candidate is the region's
+ * corrected reflectance (the paper's criterion).  The region itself comes from
+ * the user in the paper (clicks, flood fill, tracking); here it is a mask.
+ *   rgb_dev       3 x H x W float32 frame; labels_dev H x W uint8 (0..K-1)
+ *   b_init_host   K x 3 initial base colours (finite, > 0)
+ *   region_dev    H x W uint8, nonzero on the region
+ *   best_out      out, the winning label (colour index - 1)
+ *   sparsity_out  out, K doubles (i-sparsity over the region per candidate) or NULL
+ *   labels_out_dev out, H x W uint8: the labels with the region set to the winner, or NULL
+ * Creates and destroys its own K contexts; synchronises.  Errors are reported
+ * by gid_last_error(NULL). */
+int gid_correct_region(int H, int W, int K, const gid_weights* w, const float* rgb_dev, const uint8_t* labels_dev,
+                       const float* b_init_host, const uint8_t* region_dev, int n_outer, int m_inner, void* stream,
+                       int* best_out, double* sparsity_out, uint8_t* labels_out_dev);
 
 /* ---- instrumentation ---- */
 

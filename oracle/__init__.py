@@ -354,6 +354,31 @@ def cluster(I, k_max, merge_dist=0.2, max_iter=100):
     return labels, b, centres
 
 
+def region_isparsity(X, region, lambda_isparsity=DEFAULT_WEIGHTS["lambda_isparsity"]):
+    """The i-sparsity term (eq:shading-sparsity-term) summed over a region's pixels."""
+    X = _f64(X)
+    return lambda_isparsity * np.abs(X[4:])[:, np.asarray(region) != 0].sum()
+
+
+def correct_region(I, labels, b_init, region, off_s, N, M):
+    """Reflectance correction of a misclustered region (Sec. 4.2): for every
+    candidate base colour, a full decomposition (cold start, N x M) with the
+    region's pixels labelled with it; the candidate whose solution has the
+    sparsest indirect illumination over the region (smallest i-sparsity term)
+    wins.  Returns (winning label, i-sparsity per candidate)."""
+    I = _f64(I)
+    K = np.asarray(b_init).shape[0]
+    C, wsr, om, _ = precompute(I, off_s)
+    sp = []
+    for k in range(K):
+        lab = np.where(np.asarray(region) != 0, k, labels).astype(np.uint8)
+        pb = Problem(I, lab, b_init, wsr, om, off_s)
+        X, _, _ = solve_frame(pb, pb.init_cold(), N, M)
+        sp.append(region_isparsity(X, region))
+    sp = np.array(sp)
+    return int(sp.argmin()), sp
+
+
 def dense_solve(A, g):
     """Delta b (K, 3) from the three K x K blocks by SVD pseudo-inverse (Sec. 6.1)."""
     K = A.shape[1]

@@ -347,7 +347,9 @@ struct Launch {
   static void dense(const gid_ctx* c, int solve) {
     k_dense<K, true><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
   }
-  static void energy(const gid_ctx* c) { k_energy<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
+  static void energy(const gid_ctx* c, const uint8_t* mask = nullptr) {
+    k_energy<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c), mask);
+  }
   static void init_cold(const gid_ctx* c) { k_init_cold<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void fit_direct(const gid_ctx* c) { k_fit_direct<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c)); }
   static void recombine(const gid_ctx* c, const EditTable& e, const uint8_t* mask, float* out) {
@@ -870,10 +872,10 @@ extern "C" int gid_set_state(gid_ctx* c, const float* X_dev) {
   return GID_OK;
 }
 
-extern "C" int gid_energy(gid_ctx* c, double* total, double* per_term) {
+extern "C" int gid_energy_region(gid_ctx* c, const uint8_t* mask_dev, double* total, double* per_term) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
-  launch(c, GID_KIND_ENERGY, [&] { GID_DISPATCH(c, energy, c); });
+  launch(c, GID_KIND_ENERGY, [&] { GID_DISPATCH(c, energy, c, mask_dev); });
   if (int rc = check_launch(c, "k_energy")) return rc;
   double E[8];
   GID_TRY_CUDA(c, cudaMemcpyAsync(E, c->sc->energy, sizeof(E), cudaMemcpyDeviceToHost, c->stream));
@@ -885,6 +887,10 @@ extern "C" int gid_energy(gid_ctx* c, double* total, double* per_term) {
   if (rc) return rc;
   if (!std::isfinite(t)) return fail(c, GID_ERR_NUMERIC, "energy is not finite");
   return GID_OK;
+}
+
+extern "C" int gid_energy(gid_ctx* c, double* total, double* per_term) {
+  return gid_energy_region(c, nullptr, total, per_term);
 }
 
 extern "C" int gid_solve_frame_host(gid_ctx* c, const float* rgb_host, const uint8_t* labels_host, int init_mode,
@@ -1404,4 +1410,67 @@ extern "C" int gid_batch_autotune(gid_batch* b, const char* cache_path, int reps
     fclose(f);
   }
   return GID_OK;
+}
+
+// ---------------------------------------------------------------- misclustering correction
+
+extern "C" int gid_correct_region(int H, int W, int K, const gid_weights* w, const float* rgb_dev,
+                                  const uint8_t* labels_dev, const float* b_init_host, const uint8_t* region_dev,
+                                  int n_outer, int m_inner, void* stream, int* best_out, double* sparsity_out,
+                                  uint8_t* labels_out_dev) {
+  if (!rgb_dev || !labels_dev || !b_init_host || !region_dev || !best_out)
+    return fail(nullptr, GID_ERR_INVALID_ARG, "NULL argument");
+  if (K < 1 || K > GID_MAX_K || H < 1 || W < 1) return fail(nullptr, GID_ERR_INVALID_ARG, "bad H, W or K");
+  if (n_outer < 1 || m_inner < 1) return fail(nullptr, GID_ERR_INVALID_ARG, "n_outer, m_inner >= 1");
+  const long HW = (long)H * W;
+  std::vector<int> Hs(K, H), Ws(K, W), Ks(K, K);
+  gid_batch* bt = nullptr;
+  if (int rc = gid_batch_create(K, Hs.data(), Ws.data(), Ks.data(), w, 0, stream, &bt)) return rc;
+  uint8_t* labs = nullptr;
+  auto done = [&](int rc) {
+    if (labs) cudaFree(labs);
+    gid_batch_destroy(bt);
+    return rc;
+  };
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaMalloc(&labs, (size_t)K * HW) != cudaSuccess) {
+    cudaGetLastError();
+    return done(fail(nullptr, GID_ERR_OOM, "candidate labels"));
+  }
+  // candidate k: the region's pixels labelled k (base colour k + 1)
+  std::vector<const float*> rgbs(K, rgb_dev);
+  std::vector<const uint8_t*> lp(K);
+  for (int k = 0; k < K; k++) {
+    k_relabel<<<(unsigned)((HW + 255) / 256), 256, 0, s>>>(labels_dev, region_dev, (uint8_t)k, labs + k * HW, HW);
+    lp[k] = labs + k * HW;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return done(fail(nullptr, GID_ERR_CUDA, "k_relabel", cudaGetErrorString(e)));
+  for (int k = 0; k < K; k++)
+    if (int rc = gid_set_base_colors(gid_batch_ctx(bt, k), b_init_host))
+      return done(fail(nullptr, rc, "candidate base colours", gid_last_error(gid_batch_ctx(bt, k))));
+  if (int rc = gid_batch_set_frames(bt, rgbs.data(), lp.data())) return done(fail(nullptr, rc, gid_batch_last_error(bt)));
+  if (int rc = gid_batch_init(bt, 0)) return done(fail(nullptr, rc, gid_batch_last_error(bt)));
+  if (int rc = gid_batch_run(bt, n_outer, m_inner)) return done(fail(nullptr, rc, gid_batch_last_error(bt)));
+  int best = -1;
+  double best_s = 0.0;
+  for (int k = 0; k < K; k++) {
+    double tot = 0.0, per[8];
+    if (int rc = gid_energy_region(gid_batch_ctx(bt, k), region_dev, &tot, per))
+      return done(fail(nullptr, rc, "candidate energy", gid_last_error(gid_batch_ctx(bt, k))));
+    if (sparsity_out) sparsity_out[k] = per[5];
+    if (best < 0 || per[5] < best_s) {
+      best = k;
+      best_s = per[5];
+    }
+  }
+  *best_out = best;
+  if (labels_out_dev) {
+    k_relabel<<<(unsigned)((HW + 255) / 256), 256, 0, s>>>(labels_dev, region_dev, (uint8_t)best, labels_out_dev, HW);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return done(fail(nullptr, GID_ERR_CUDA, "k_relabel", cudaGetErrorString(e)));
+  }
+  return done(GID_OK);
 }

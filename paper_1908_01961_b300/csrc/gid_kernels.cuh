@@ -1352,16 +1352,20 @@ __global__ void __launch_bounds__(256) k_dense(Params P, int solve) {
   }
 }
 
-// Exact energy (eq:giv-energy), 8 FP64 sums into sc->energy.
+// Exact energy (eq:giv-energy), 8 FP64 sums into sc->energy; with a mask, the
+// terms evaluated at the masked pixels only (each pixel owns its data,
+// clustering, monochrome, i-sparsity and non-neg terms and the pair / edge
+// terms evaluated at it).
 template <int K>
-__global__ void __launch_bounds__(NT) k_energy(Params P) {
+__global__ void __launch_bounds__(NT) k_energy(Params P, const uint8_t* __restrict__ mask) {
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
   const Weights& w = P.w;
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
   float E[8];
   for (int i = 0; i < 8; i++) E[i] = 0.f;
-  if (x < P.W && y < P.H) {
+  // with a mask (H x W, dense): only the terms evaluated at its nonzero pixels
+  if (x < P.W && y < P.H && (!mask || mask[(long)y * P.W + x])) {
     const long o = off2(P, y, x);
     PixState<K> s;
     load_state<K>(P, ct, o, s);
@@ -1441,6 +1445,13 @@ __global__ void k_readout(Params P, float* __restrict__ Rout, float* __restrict_
     for (int c = 0; c < 3; c++) Rout[c * HW + dst] = expf(P.X[c * P.plane + o]);
   if (Tout)
     for (int k = 0; k <= K; k++) Tout[k * HW + dst] = P.X[(3 + k) * P.plane + o];
+}
+
+// Labels of one correction candidate: region pixels (mask != 0) take label k.
+__global__ void k_relabel(const uint8_t* __restrict__ lab, const uint8_t* __restrict__ region, uint8_t k,
+                          uint8_t* __restrict__ out, long n) {
+  const long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = region[i] ? k : lab[i];
 }
 
 // ---------------------------------------------------------------- editing

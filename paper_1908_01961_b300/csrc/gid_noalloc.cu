@@ -27,10 +27,12 @@
 #define k_ingest k_ingest_noalloc_tu
 #define k_prior_weights k_prior_weights_noalloc_tu
 #define k_reset_colors k_reset_colors_noalloc_tu
+#define k_relabel k_relabel_noalloc_tu
 #include "gid_kernels.cuh"
 #undef k_ingest
 #undef k_prior_weights
 #undef k_reset_colors
+#undef k_relabel
 
 using namespace gid;
 

@@ -35,7 +35,7 @@ EXPORTS = (
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
     "gid_net_set_weights", "gid_net_get_weights", "gid_net_get_grads", "gid_net_forward", "gid_net_backward",
     "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned", "gid_base_color_step",
-    "gid_solve_video_host", "gid_recombine", "gid_cluster",
+    "gid_solve_video_host", "gid_recombine", "gid_cluster", "gid_energy_region", "gid_correct_region",
 )
 
 
@@ -135,6 +135,8 @@ def load():
     L.gid_solve_video_host.argtypes = [P, I, P, P, I, I, I, P, P, P]
     L.gid_recombine.argtypes = [P, F, F, P, P]
     L.gid_cluster.argtypes = [I, I, P, I, ctypes.c_float, P, P, F, ctypes.POINTER(I), ctypes.c_char_p, I]
+    L.gid_energy_region.argtypes = [P, P, D, D]
+    L.gid_correct_region.argtypes = [I, I, I, ctypes.POINTER(Weights), P, P, F, P, I, I, P, ctypes.POINTER(I), D, P]
     for n in EXPORTS:
         if n not in ("gid_default_weights", "gid_destroy", "gid_last_error", "gid_batch_destroy",
                      "gid_batch_last_error", "gid_batch_ctx", "gid_net_destroy", "gid_net_last_error",
@@ -198,6 +200,29 @@ def cluster(rgb, k_max=10, merge_dist=0.2, labels=None, stream=None):
     if rc != GID_OK:
         raise GidError(rc, err.value.decode())
     return labels, b[:k.value].copy()
+
+
+def correct_region(rgb, labels, b_init, region, weights=None, n_outer=8, m_inner=20, stream=None):
+    """Misclustering correction of a region (gid_correct_region): rgb (3, H, W)
+    float32, labels and region (H, W) uint8 CUDA tensors, b_init (K, 3).
+    Returns (winning label, i-sparsity per candidate (K,), corrected labels)."""
+    import torch
+    _, H, W = rgb.shape
+    b = np.ascontiguousarray(b_init, np.float32)
+    K = b.shape[0]
+    w = weights if weights is not None else default_weights()
+    best = ctypes.c_int()
+    sp = np.zeros(K)
+    out = torch.empty((H, W), dtype=torch.uint8, device=rgb.device)
+    s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    L = load()
+    rc = L.gid_correct_region(H, W, K, ctypes.byref(w), _ptr(rgb), _ptr(labels),
+                              b.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), _ptr(region), n_outer, m_inner,
+                              ctypes.c_void_p(s), ctypes.byref(best), sp.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                              _ptr(out))
+    if rc != GID_OK:
+        raise GidError(rc, L.gid_last_error(None).decode())
+    return best.value, sp, out
 
 
 def _ptr(t):
@@ -315,6 +340,14 @@ class Solver:
         tot = ctypes.c_double()
         per = (ctypes.c_double * 8)()
         self._chk(self.lib.gid_energy(self.h, ctypes.byref(tot), per))
+        return tot.value, np.array(per[:])
+
+    def energy_region(self, mask):
+        """Energy terms evaluated at the pixels where the (H, W) uint8 CUDA mask is nonzero."""
+        self._check_dev(mask, (self.H, self.W), self.torch.uint8)
+        tot = ctypes.c_double()
+        per = (ctypes.c_double * 8)()
+        self._chk(self.lib.gid_energy_region(self.h, _ptr(mask), ctypes.byref(tot), per))
         return tot.value, np.array(per[:])
 
     def solve_frame_host(self, rgb, labels, init_mode, n_outer, m_inner, R=None, T=None, b=None):
