@@ -247,6 +247,27 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
  * agree to FP32 rounding order; only speed differs. */
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
+/* ---- preconditioner ---- */
+
+/* Sec. 6.1 solves each Gauss-Newton system by preconditioned conjugate
+ * gradient without naming the preconditioner.  GID_PRECOND_JACOBI (default):
+ * M = diag(J^T J).  GID_PRECOND_BLOCK: M = the per-pixel (K+4) x (K+4) diagonal
+ * blocks of J^T J (the unknowns r_R, r_G, r_B, T_0..T_K of one pixel coupled
+ * through the data and monochrome terms), factored once per Gauss-Newton step
+ * by an FP32 Cholesky per pixel (a pixel whose block rounding made indefinite
+ * falls back to its diagonal).  The block form stores (K+4)(K+5)/2 extra planes
+ * (allocated on the first switch; GID_ERR_OOM if that fails) and always runs
+ * one operator and one vector kernel per PCG step (the persistent loop of
+ * gid_set_apply_tile(0) is Jacobi only).  Synchronises the context's streams
+ * and drops its cached graphs.  A batch captures its graph on its first run:
+ * set the preconditioner of its contexts (gid_batch_ctx) before that. */
+#define GID_PRECOND_JACOBI 0
+#define GID_PRECOND_BLOCK 1
+int gid_set_preconditioner(gid_ctx* ctx, int kind);
+
+/* The context's preconditioner (GID_PRECOND_*), -1 for a NULL ctx. */
+int gid_get_preconditioner(const gid_ctx* ctx);
+
 /* Time reps PCG steps with each of the five ways above on the current frame
  * and state (CUDA events on the context stream) and keep the fastest.  Writes
  * the chosen rows (0 = persistent) to *rows_out and the five timings (us per

@@ -64,6 +64,9 @@ def lib():
         _lib.or_energy.argtypes = [P, D, D]
         _lib.or_pcg.argtypes = [P, D, ctypes.c_int, D, D]
         _lib.or_gn_step.argtypes = [P, D, ctypes.c_int]
+        _lib.or_block_diag.argtypes = [P, D, D, ctypes.c_uint, D]
+        _lib.or_pcg_variant.argtypes = [P, D, ctypes.c_int, ctypes.c_int, ctypes.c_int, D, D]
+        _lib.or_pcg_variant.restype = ctypes.c_int
         _lib.or_dense_normal.argtypes = [P, D, D, D]
         _lib.or_init_cold.argtypes = [P, D]
         _lib.or_precompute.argtypes = [ctypes.c_int, ctypes.c_int, D, D, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -224,6 +227,25 @@ class Problem:
         delta = np.zeros(self.shape)
         rz = np.zeros(M + 1)
         lib().or_pcg(self.ptr, _d(X), int(M), _d(delta), _d(rz))
+        return delta, rz
+
+    def block_diag(self, X, Xw=None, mask=ALL):
+        """Per-pixel (V, V) diagonal blocks of J^T J, shape (H, W, V, V)."""
+        X = self._x(X)
+        Xw = X if Xw is None else self._x(Xw)
+        V = self.shape[0]
+        B = np.zeros((self.shape[1], self.shape[2], V, V))
+        lib().or_block_diag(self.ptr, _d(X), _d(Xw), mask, _d(B))
+        return B
+
+    def pcg_variant(self, X, M, block=False, single_reduction=False):
+        """M PCG steps with the Jacobi or block-Jacobi preconditioner, in the
+        textbook or the single-reduction recurrence (returns delta, rho history)."""
+        X = self._x(X)
+        delta = np.zeros(self.shape)
+        rz = np.zeros(M + 1)
+        if not lib().or_pcg_variant(self.ptr, _d(X), int(M), int(block), int(single_reduction), _d(delta), _d(rz)):
+            raise ArithmeticError("a diagonal block is not positive definite")
         return delta, rz
 
     def gn_step(self, X, M):
@@ -390,15 +412,16 @@ def dense_solve(A, g):
     return db
 
 
-def solve_frame(pb: Problem, X, N: int, M: int, refine: bool = True):
+def solve_frame(pb: Problem, X, N: int, M: int, refine: bool = True, block: bool = False):
     """N outer flip-flop iterations (Sec. 6.1): a Gauss-Newton step on the layers
     (M PCG steps) with the base colours fixed, then the base-colour step with the
     layers fixed.  Returns the final X, b and the exact energy after each outer
-    iteration (energy history has N + 1 rows, row 0 at the initial state)."""
+    iteration (energy history has N + 1 rows, row 0 at the initial state).
+    block: the PCG steps use the block-Jacobi preconditioner instead of Jacobi."""
     X = _f64(X).copy()
     hist = [pb.energy(X)]
     for _ in range(N):
-        X = pb.gn_step(X, M)
+        X = X + pb.pcg_variant(X, M, block=True)[0] if block else pb.gn_step(X, M)
         if refine:
             A, g = pb.dense_normal(X)
             pb.set_b(pb.b_init + dense_solve(A, g))

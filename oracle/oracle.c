@@ -416,6 +416,160 @@ void or_gn_step(const or_problem *pb, double *X, int M) {
   free(delta);
 }
 
+/* ---------------- preconditioner and PCG variants (Sec. 6.1 leaves the preconditioner unnamed) ---------------- */
+
+/*
+ * Per-pixel V x V diagonal blocks of J^T J: B[x][u][v] = sum over the rows of
+ * a_(u,x) a_(v,x), both entries of one row at the same pixel x.  B is (P, V, V),
+ * row-major per pixel.  The diagonal of B is or_diag's d.
+ */
+typedef struct { double *B; long P; int V; } block_ctx;
+static void visit_block(const or_row *r, void *vc) {
+  block_ctx *c = (block_ctx *)vc;
+  for (int i = 0; i < r->n; i++)
+    for (int j = 0; j < r->n; j++) {
+      long xi = r->j[i] % c->P, xj = r->j[j] % c->P;
+      if (xi != xj) continue;
+      int u = (int)(r->j[i] / c->P), v = (int)(r->j[j] / c->P);
+      c->B[(xi * c->V + u) * c->V + v] += r->a[i] * r->a[j];
+    }
+}
+
+void or_block_diag(const or_problem *pb, const double *X, const double *Xw, unsigned mask, double *B) {
+  const int V = pb->K + 4;
+  memset(B, 0, sizeof(double) * P_of(pb) * V * V);
+  block_ctx c = {B, P_of(pb), V};
+  or_rows(pb, X, Xw, mask, visit_block, &c);
+}
+
+/* Cholesky factor (lower, in place, row-major n x n) of an SPD matrix; returns 0 on a non-positive pivot. */
+static int cholesky(double *A, int n) {
+  for (int j = 0; j < n; j++) {
+    double s = A[j * n + j];
+    for (int k = 0; k < j; k++) s -= A[j * n + k] * A[j * n + k];
+    if (!(s > 0)) return 0;
+    A[j * n + j] = sqrt(s);
+    for (int i = j + 1; i < n; i++) {
+      double t = A[i * n + j];
+      for (int k = 0; k < j; k++) t -= A[i * n + k] * A[j * n + k];
+      A[i * n + j] = t / A[j * n + j];
+    }
+  }
+  return 1;
+}
+
+/* Solve L L^T z = r with the factor from cholesky(). */
+static void chol_solve(const double *L, int n, const double *r, double *z) {
+  for (int i = 0; i < n; i++) {
+    double t = r[i];
+    for (int k = 0; k < i; k++) t -= L[i * n + k] * z[k];
+    z[i] = t / L[i * n + i];
+  }
+  for (int i = n - 1; i >= 0; i--) {
+    double t = z[i];
+    for (int k = i + 1; k < n; k++) t -= L[k * n + i] * z[k];
+    z[i] = t / L[i * n + i];
+  }
+}
+
+/* The preconditioner step z = M^-1 r: Jacobi (block == 0: d = diag J^T J) or
+ * block-Jacobi (block == 1: Lb = the per-pixel Cholesky factors of or_block_diag). */
+typedef struct { int block; long P; int V; const double *d, *Lb; } precond;
+static void precond_apply(const precond *m, const double *r, double *z) {
+  if (!m->block) {
+    for (long i = 0; i < m->P * m->V; i++) z[i] = r[i] / m->d[i];
+    return;
+  }
+  double rv[32], zv[32];
+  for (long x = 0; x < m->P; x++) {
+    for (int v = 0; v < m->V; v++) rv[v] = r[v * m->P + x];
+    chol_solve(m->Lb + x * m->V * m->V, m->V, rv, zv);
+    for (int v = 0; v < m->V; v++) z[v * m->P + x] = zv[v];
+  }
+}
+
+/*
+ * M steps of preconditioned CG on J^T J delta = -J^T F at X, delta_0 = 0, no early
+ * exit, in one of two preconditioners (block: 0 Jacobi, 1 block-Jacobi) and two
+ * recurrences (single_reduction: 0 the textbook two-reduction recurrence, as in
+ * or_pcg; 1 the single-reduction recurrence of Chronopoulos and Gear (1989),
+ * which carries s = A p and takes <r,u> and <A u,u> from one reduction, u = M^-1 r:
+ *   beta = gamma / gamma_old, alpha = gamma / (delta - beta gamma / alpha_old),
+ *   p = u + beta p, s = w + beta s, x += alpha p, r -= alpha s, u = M^-1 r, w = A u).
+ * In exact arithmetic both recurrences give the same iterates.  rz[m] = <r_m, z_m>
+ * (length M + 1, may be NULL).  Returns 0 if a block is not positive definite.
+ */
+int or_pcg_variant(const or_problem *pb, const double *X, int M, int block, int single_reduction, double *delta,
+                   double *rz) {
+  const long n = nvar(pb), P = P_of(pb);
+  const int V = pb->K + 4;
+  double *g = malloc(sizeof(double) * n), *d = malloc(sizeof(double) * n);
+  double *r = malloc(sizeof(double) * n), *z = malloc(sizeof(double) * n);
+  double *p = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
+  double *w = malloc(sizeof(double) * n), *Lb = NULL;
+  int ok = 1;
+  or_rhs(pb, X, X, ALL_TERMS, g);
+  or_diag(pb, X, X, ALL_TERMS, d);
+  if (block) {
+    Lb = malloc(sizeof(double) * P * V * V);
+    or_block_diag(pb, X, X, ALL_TERMS, Lb);
+    for (long x = 0; x < P && ok; x++) ok = cholesky(Lb + x * V * V, V);
+  }
+  precond m = {block, P, V, d, Lb};
+  for (long i = 0; i < n; i++) {
+    delta[i] = 0;
+    r[i] = g[i];
+  }
+  if (ok && !single_reduction) {
+    precond_apply(&m, r, z);
+    for (long i = 0; i < n; i++) p[i] = z[i];
+    double rho = dot(r, z, n);
+    if (rz) rz[0] = rho;
+    for (int it = 1; it <= M; it++) {
+      or_apply(pb, X, X, ALL_TERMS, p, q);
+      double pq = dot(p, q, n);
+      double alpha = pq != 0 ? rho / pq : 0.0;
+      for (long i = 0; i < n; i++) {
+        delta[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+      }
+      precond_apply(&m, r, z);
+      double rho_new = dot(r, z, n);
+      double beta = rho != 0 ? rho_new / rho : 0.0;
+      for (long i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
+      rho = rho_new;
+      if (rz) rz[it] = rho;
+    }
+  } else if (ok) {
+    /* z holds u = M^-1 r, w = A u, q holds s = A p */
+    precond_apply(&m, r, z);
+    or_apply(pb, X, X, ALL_TERMS, z, w);
+    double gamma = dot(r, z, n), dl = dot(w, z, n);
+    double alpha = dl != 0 ? gamma / dl : 0.0, beta = 0.0, gamma_old = gamma;
+    if (rz) rz[0] = gamma;
+    for (long i = 0; i < n; i++) p[i] = q[i] = 0;
+    for (int it = 1; it <= M; it++) {
+      for (long i = 0; i < n; i++) {
+        p[i] = z[i] + beta * p[i];
+        q[i] = w[i] + beta * q[i];
+        delta[i] += alpha * p[i];
+        r[i] -= alpha * q[i];
+      }
+      precond_apply(&m, r, z);
+      or_apply(pb, X, X, ALL_TERMS, z, w);
+      gamma = dot(r, z, n);
+      dl = dot(w, z, n);
+      if (rz) rz[it] = gamma;
+      beta = gamma_old != 0 ? gamma / gamma_old : 0.0;
+      double den = dl - (alpha != 0 ? beta * gamma / alpha : 0.0);
+      alpha = den != 0 ? gamma / den : 0.0;
+      gamma_old = gamma;
+    }
+  }
+  free(g); free(d); free(r); free(z); free(p); free(q); free(w); free(Lb);
+  return ok;
+}
+
 /* ---------------- dense step: base-colour refinement (Sec. 5.4) ---------------- */
 
 /*

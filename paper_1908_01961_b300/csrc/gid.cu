@@ -58,6 +58,9 @@ struct gid_ctx {
   int upd_cap = 148 * 4;   // vector-step blocks resident at once (SMs x blocks per SM)
   int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
+  int precond = 0;          // GID_PRECOND_JACOBI or GID_PRECOND_BLOCK (gid_set_preconditioner)
+  float* blk = nullptr;     // block-Jacobi factors, V (V + 1) / 2 planes (allocated on first use)
+  int blk_blocks = 0;       // grid of the block-Jacobi vector step
   // CUDA graphs of gid_run's launch sequence, replayed on a context-owned stream
   struct Graph {
     int n, m, refine, temporal, th;
@@ -173,6 +176,7 @@ static Params params(const gid_ctx* c) {
   P.q = c->q;
   P.Minv = c->Minv;
   P.coef = c->coef;
+  P.blk = c->blk;
   P.col = c->col;
   P.sc = c->sc;
   P.partial = c->partial;
@@ -197,6 +201,8 @@ static int update_blocks(const gid_ctx* c) {
   const long items = (long)c->V * (c->plane / 4);
   return (int)std::max(1L, std::min((items + 255) / 256, (long)c->upd_cap));
 }
+// Blocks of the PCG vector step that writes the <r, z> partials the next operator step reads.
+static int vector_blocks(const gid_ctx* c) { return c->precond ? c->blk_blocks : update_blocks(c); }
 
 // ---------------------------------------------------------------- TMA tensor maps
 
@@ -275,7 +281,7 @@ struct Launch {
       const_cast<gid_ctx*>(c)->map_failed = true;
       return;
     }
-    launch_pdl(c, k_apply<K, TH>, grid, dim3(BX, TH), smem, params(c), mode, first, it, update_blocks(c), pin, pout,
+    launch_pdl(c, k_apply<K, TH>, grid, dim3(BX, TH), smem, params(c), mode, first, it, vector_blocks(c), pin, pout,
                qout, m->r, m->t);
   }
   // Opt every operator tile shape in to its dynamic shared memory (before any graph capture).
@@ -343,6 +349,23 @@ struct Launch {
   }
   static void update(const gid_ctx* c, int it, const float* p, int last) {
     launch_pdl(c, k_update<K>, dim3(update_blocks(c)), dim3(256), 0, params(c), it, apply_blocks(c), p, last);
+  }
+  // Block-Jacobi: the factorisation and PCG start, and the vector step.
+  static void block_factor(const gid_ctx* c) {
+    k_block_factor<K><<<pix_grid(c), dim3(BX, BY), 0, c->stream>>>(params(c));
+  }
+  static void update_block(const gid_ctx* c, int it, const float* p, int last) {
+    launch_pdl(c, k_update_block<K>, dim3(c->blk_blocks), dim3(256), 0, params(c), it, apply_blocks(c), p, last);
+  }
+  // Resident blocks of the block-Jacobi vector step (SMs x blocks per SM).
+  static int block_capacity(const gid_ctx*) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update_block<K>, 256, 0) != cudaSuccess ||
+        per_sm < 1 || sms < 1)
+      return 148 * 2;
+    return sms * per_sm;
   }
   static void dense(const gid_ctx* c, int solve) {
     k_dense<K, true><<<dim3(dense_blocks(c), 3), 256, 0, c->stream>>>(params(c), solve);
@@ -583,6 +606,7 @@ extern "C" void gid_destroy(gid_ctx* c) {
     cudaEventDestroy(c->gev_out);
   }
   cudaFree(c->pool);
+  cudaFree(c->blk);
   cudaFree(c->st_rgb);
   cudaFree(c->st_lab);
   cudaFree(c->st_R);
@@ -718,6 +742,18 @@ extern "C" int gid_init_learned(gid_ctx* c, gid_net* net, float zero_below) {
 }
 
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
+  if (c->precond == GID_PRECOND_BLOCK) {
+    launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 3, (float*)nullptr, (float*)nullptr); });
+    launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, block_factor, c); });
+    if (int rc = check_launch(c, "k_linearize / k_block_factor")) return rc;
+    for (int m = 1; m <= m_inner; m++) {
+      launch(c, GID_KIND_APPLY,
+             [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, m, (const float*)c->pA, c->pA, c->q); });
+      launch(c, GID_KIND_UPDATE,
+             [&] { GID_DISPATCH(c, update_block, c, m, (const float*)c->pA, m == m_inner ? last_mode : 0); });
+    }
+    return check_launch(c, "pcg (block-Jacobi)");
+  }
   launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
   if (int rc = check_launch(c, "k_linearize")) return rc;
   if (c->persistent && c->pcg_blocks > 0) {
@@ -1103,6 +1139,48 @@ extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
   c->persistent = false;
   return GID_OK;
 }
+
+// ---------------------------------------------------------------- preconditioner
+
+extern "C" int gid_set_preconditioner(gid_ctx* c, int kind) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (kind != GID_PRECOND_JACOBI && kind != GID_PRECOND_BLOCK)
+    return fail(c, GID_ERR_INVALID_ARG, "preconditioner must be GID_PRECOND_JACOBI or GID_PRECOND_BLOCK");
+  if (kind == c->precond) return GID_OK;
+  if (kind == GID_PRECOND_BLOCK && !c->blk) {
+    const size_t nb = (size_t)c->V * (c->V + 1) / 2;
+    if (cudaMalloc(&c->blk, nb * c->plane * sizeof(float)) != cudaSuccess) {
+      cudaGetLastError();
+      c->blk = nullptr;
+      return fail(c, GID_ERR_OOM, "block-Jacobi factor planes");
+    }
+    int cap = 0;
+    switch (c->K) {
+      case 1: cap = Launch<1>::block_capacity(c); break;
+      case 2: cap = Launch<2>::block_capacity(c); break;
+      case 3: cap = Launch<3>::block_capacity(c); break;
+      case 4: cap = Launch<4>::block_capacity(c); break;
+      case 5: cap = Launch<5>::block_capacity(c); break;
+      case 6: cap = Launch<6>::block_capacity(c); break;
+      case 7: cap = Launch<7>::block_capacity(c); break;
+      case 8: cap = Launch<8>::block_capacity(c); break;
+      case 9: cap = Launch<9>::block_capacity(c); break;
+      default: cap = Launch<10>::block_capacity(c); break;
+    }
+    // one pixel per thread; never more blocks than the partial slots hold
+    const long want = (c->plane + 255) / 256;
+    c->blk_blocks = (int)std::max(1L, std::min({want, (long)cap, (long)c->nbmax}));
+  }
+  // the cached graphs hold the other preconditioner's launch sequence
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->gs) cudaStreamSynchronize(c->gs);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  c->precond = kind;
+  return GID_OK;
+}
+
+extern "C" int gid_get_preconditioner(const gid_ctx* c) { return c ? c->precond : -1; }
 
 extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) {
   if (!c || reps < 1) return fail(c, GID_ERR_INVALID_ARG, "bad argument");

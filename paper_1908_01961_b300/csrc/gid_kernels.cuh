@@ -76,6 +76,7 @@ struct Params {
   float* q;
   float* Minv;
   float* coef;  // operator coefficient planes written by k_linearize (CoefLayout)
+  float* blk;   // block-Jacobi: packed Cholesky factors, V (V + 1) / 2 planes (k_block_factor)
   DevColors* col;
   DevScalars* sc;
   double* partial;
@@ -506,7 +507,9 @@ __device__ __forceinline__ void load_state(const Params& P, const ColorTable<K>&
 // residual r = g itself is not stored);
 // the operator coefficients of the step (CoefLayout) in every mode.
 // mode 0: PCG init (writes z, Minv, zero delta, rho); mode 1: stage output
-// (writes g to gout and diag to dout); mode 2: coefficients only.
+// (writes g to gout and diag to dout); mode 2: coefficients only; mode 3:
+// block-Jacobi start (writes g to z, diag to Minv, zero delta; k_block_factor
+// completes the PCG init).
 template <int K>
 __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int mode, float* __restrict__ gout,
                                                   float* __restrict__ dout,
@@ -660,6 +663,14 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
         P.z[ov] = zz;
         P.d[ov] = 0.f;
         rz += g[v] * zz;
+      }
+    } else if (mode == 3) {
+#pragma unroll
+      for (int v = 0; v < V; v++) {
+        const long ov = v * P.plane + o;
+        P.Minv[ov] = dg[v];
+        P.z[ov] = g[v];
+        P.d[ov] = 0.f;
       }
     } else if (mode == 1) {
 #pragma unroll
@@ -1094,6 +1105,205 @@ __global__ void __launch_bounds__(256, 4) k_update(Params P, int it, int nb_prev
   const float rz = update_range<K>(P, p, alpha, last, (long)blockIdx.x * blockDim.x + threadIdx.x,
                                    (long)gridDim.x * blockDim.x);
   if (last) return;
+  const double bs = block_sum_f(rz);
+  if (threadIdx.x == 0) pcg_partials(P, PART_RZ, it)[blockIdx.x] = bs;
+}
+
+// ---------------------------------------------------------------- block-Jacobi preconditioner
+
+// Sec. 6.1 names no preconditioner.  Besides the Jacobi default this file offers
+// the per-pixel block-Jacobi one: M = blockdiag_x B(x), B(x) the V x V diagonal
+// block of J^T J at pixel x.  Only the rows that touch several unknowns of one
+// pixel put entries off its diagonal: the three data rows (r_c with every T_k,
+// T_k with T_l) and the three monochrome rows (T_k with T_l); every other term
+// adds to the diagonal alone.  Variables in plane order r_0..r_2, T_0..T_K;
+// packed lower triangle, entry (i, j), j <= i, at i (i + 1) / 2 + j.
+__host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
+
+// In-register Cholesky B = L L^T of a packed SPD block.  A pivot that is not
+// positive (a block that rounding made indefinite) turns the whole block into
+// its diagonal, i.e. that pixel falls back to Jacobi.
+template <int V>
+__device__ __forceinline__ void block_cholesky(float (&L)[V * (V + 1) / 2]) {
+  float dg[V];
+#pragma unroll
+  for (int i = 0; i < V; i++) dg[i] = L[tri(i, i)];
+  bool ok = true;
+#pragma unroll
+  for (int j = 0; j < V; j++) {
+    float s = L[tri(j, j)];
+#pragma unroll
+    for (int k = 0; k < j; k++) s = fmaf(-L[tri(j, k)], L[tri(j, k)], s);
+    ok = ok && s > 0.f;
+    const float ljj = sqrtf(fmaxf(s, 1e-30f)), inv = 1.0f / ljj;
+    L[tri(j, j)] = ljj;
+#pragma unroll
+    for (int i = j + 1; i < V; i++) {
+      float t = L[tri(i, j)];
+#pragma unroll
+      for (int k = 0; k < j; k++) t = fmaf(-L[tri(i, k)], L[tri(j, k)], t);
+      L[tri(i, j)] = t * inv;
+    }
+  }
+  if (!ok) {
+#pragma unroll
+    for (int i = 0; i < V; i++)
+#pragma unroll
+      for (int j = 0; j <= i; j++) L[tri(i, j)] = i == j ? sqrtf(dg[i]) : 0.f;
+  }
+}
+
+// y = (L L^T)^-1 r by forward and back substitution (r and y may be one array).
+template <int V>
+__device__ __forceinline__ void block_solve(const float (&L)[V * (V + 1) / 2], const float (&r)[V], float (&y)[V]) {
+#pragma unroll
+  for (int i = 0; i < V; i++) {
+    float t = r[i];
+#pragma unroll
+    for (int k = 0; k < i; k++) t = fmaf(-L[tri(i, k)], y[k], t);
+    y[i] = t / L[tri(i, i)];
+  }
+#pragma unroll
+  for (int i = V - 1; i >= 0; i--) {
+    float t = y[i];
+#pragma unroll
+    for (int k = i + 1; k < V; k++) t = fmaf(-L[tri(k, i)], y[k], t);
+    y[i] = t / L[tri(i, i)];
+  }
+}
+
+// |L^T z|^2 = z^T B z.
+template <int V>
+__device__ __forceinline__ float block_norm2(const float (&L)[V * (V + 1) / 2], const float (&z)[V]) {
+  float s = 0.f;
+#pragma unroll
+  for (int j = 0; j < V; j++) {
+    float t = 0.f;
+#pragma unroll
+    for (int i = j; i < V; i++) t = fmaf(L[tri(i, j)], z[i], t);
+    s = fmaf(t, t, s);
+  }
+  return s;
+}
+
+// Block-Jacobi PCG start, after k_linearize mode 3 (g in z, diag J^T J in Minv):
+// build B(x) from that diagonal and the step's coefficient planes (A_c =
+// l_data R_c^2, S_c, the monochrome weight), factor it, store the factor
+// (P.blk), z = B^-1 g, rho = <g, z>.
+template <int K>
+__global__ void __launch_bounds__(NT) k_block_factor(Params P) {
+  constexpr int V = K + 4, NB = V * (V + 1) / 2;
+  using CL = CoefLayout<K>;
+  __shared__ ColorTable<K> ct;
+  load_colors<K>(ct, P.col);
+  const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
+  float rz = 0.f;
+  if (x < P.W && y < P.H) {
+    const long o = off2(P, y, x);
+    const float* cf = P.coef + o;
+    float A[3], S[3];
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      A[c] = cf[(CL::A + c) * P.plane];
+      S[c] = cf[(CL::S + c) * P.plane];
+    }
+    const float wm = cf[CL::WM * P.plane];
+    float L[NB];
+#pragma unroll
+    for (int i = 0; i < V; i++) L[tri(i, i)] = P.Minv[i * P.plane + o];
+    L[tri(1, 0)] = L[tri(2, 0)] = L[tri(2, 1)] = 0.f;
+#pragma unroll
+    for (int k = 0; k <= K; k++) {
+#pragma unroll
+      for (int c = 0; c < 3; c++) L[tri(3 + k, c)] = A[c] * S[c] * ct.b[k][c];
+#pragma unroll
+      for (int l = 0; l < k; l++) {
+        float t = 0.f, m = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; c++) {
+          t = fmaf(A[c] * ct.b[k][c], ct.b[l][c], t);
+          m = fmaf(ct.dm[k][c], ct.dm[l][c], m);
+        }
+        L[tri(3 + k, 3 + l)] = fmaf(wm, m, t);
+      }
+    }
+    float g[V], z[V];
+#pragma unroll
+    for (int v = 0; v < V; v++) g[v] = P.z[v * P.plane + o];
+    block_cholesky<V>(L);
+#pragma unroll
+    for (int j = 0; j < NB; j++) P.blk[j * P.plane + o] = L[j];
+    block_solve<V>(L, g, z);
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      P.z[v * P.plane + o] = z[v];
+      rz = fmaf(g[v], z[v], rz);
+    }
+  }
+  const double bs = block_sum_f(rz);
+  const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x;
+  if (tid_flat() == 0) P.partial[b] = bs;
+  if (last_block(&P.sc->cnt[CNT_LIN])) {
+    const double t = grid_total(P.partial, nb, 1, 0);
+    if (tid_flat() == 0) {
+      P.sc->rho = t;
+      P.sc->rho2[1] = t;  // rho of PCG step 1
+      P.sc->beta = 0.0;
+      P.sc->cnt[CNT_GRID] = 0u;
+    }
+  }
+}
+
+// Block-Jacobi PCG vector step it: alpha = rho / <p, q>; delta += alpha p,
+// z -= alpha B^-1 q (= B^-1 (r - alpha q); r is not stored), block partials of
+// rho' = <r', z'> = z'^T B z' = |L^T z'|^2.  One pixel per thread, grid-strided
+// over the pitched plane (padding columns skipped: their entries are zero).
+// last 1 / 2 as for k_update (they do not involve the preconditioner).  Each
+// thread holds a whole factor in registers: two blocks per SM up to K = 4, one
+// above (a factor of 55 to 105 floats).
+template <int K>
+__global__ void __launch_bounds__(256, K <= 4 ? 2 : 1)
+    k_update_block(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
+  constexpr int V = K + 4, NB = V * (V + 1) / 2;
+  grid_dep_wait();  // the operator step's p, q and partials
+  grid_dep_release();
+  const double pq = block_total(part_share(pcg_partials(P, PART_PQ, it), nb_prev));
+  const float alpha = pq != 0.0 ? (float)(P.sc->rho2[it & 1] / pq) : 0.f;
+  if (last) {
+    update_range<K>(P, p, alpha, last, (long)blockIdx.x * blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x);
+    return;
+  }
+  // Distinct planes: every load of a pixel is issued before its first store.
+  // The factors are read once per step and streamed past L2 (evict first), like
+  // delta, so that the operator step's planes stay resident.
+  const float* __restrict__ blk = P.blk;
+  const float* __restrict__ qv = P.q;
+  float* __restrict__ dv = P.d;
+  float* __restrict__ zv = P.z;
+  const long plane = P.plane;
+  float rz = 0.f;
+  const unsigned pitch = (unsigned)P.pitch, W = (unsigned)P.W;
+  for (long o = (long)blockIdx.x * blockDim.x + threadIdx.x; o < plane; o += (long)gridDim.x * blockDim.x) {
+    if ((unsigned)o % pitch >= W) continue;
+    float L[NB], y[V], pp[V], dd[V], z[V];
+#pragma unroll
+    for (int j = 0; j < NB; j++) L[j] = __ldcs(blk + j * plane + o);
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      y[v] = qv[v * plane + o];
+      pp[v] = p[v * plane + o];
+      dd[v] = __ldcs(dv + v * plane + o);
+      z[v] = zv[v * plane + o];
+    }
+    block_solve<V>(L, y, y);
+#pragma unroll
+    for (int v = 0; v < V; v++) {
+      z[v] = fmaf(-alpha, y[v], z[v]);
+      __stcs(dv + v * plane + o, fmaf(alpha, pp[v], dd[v]));
+      zv[v * plane + o] = z[v];
+    }
+    rz += block_norm2<V>(L, z);
+  }
   const double bs = block_sum_f(rz);
   if (threadIdx.x == 0) pcg_partials(P, PART_RZ, it)[blockIdx.x] = bs;
 }

@@ -16,6 +16,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libgid.so")
 
 GID_OK = 0
+PRECOND_JACOBI, PRECOND_BLOCK = 0, 1
 ERRORS = {-1: "GID_ERR_INVALID_ARG", -2: "GID_ERR_CUDA", -3: "GID_ERR_OOM", -4: "GID_ERR_STATE",
           -5: "GID_ERR_TIMEOUT", -6: "GID_ERR_NUMERIC"}
 MAX_K = 10
@@ -30,6 +31,7 @@ EXPORTS = (
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
+    "gid_set_preconditioner", "gid_get_preconditioner",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
     "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
@@ -97,6 +99,8 @@ def load():
     L.gid_profile.argtypes = [P, I]
     L.gid_profile_read.argtypes = [P, D, LL]
     L.gid_set_apply_tile.argtypes = [P, I]
+    L.gid_set_preconditioner.argtypes = [P, I]
+    L.gid_get_preconditioner.argtypes = [P]
     L.gid_set_graphs.argtypes = [P, I]
     L.gid_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), F]
     L.gid_dense_refine_noalloc.argtypes = [I, I, I, P, P, F, ctypes.POINTER(Weights), P, P, P, P,
@@ -401,6 +405,14 @@ class Solver:
     # -- operator tile shape
     def set_apply_tile(self, rows: int):
         self._chk(self.lib.gid_set_apply_tile(self.h, rows))
+
+    def set_preconditioner(self, kind: str):
+        """'jacobi' (default) or 'block' (per-pixel diagonal blocks of J^T J)."""
+        k = {"jacobi": PRECOND_JACOBI, "block": PRECOND_BLOCK}[kind]
+        self._chk(self.lib.gid_set_preconditioner(self.h, k))
+
+    def preconditioner(self) -> str:
+        return ("jacobi", "block")[self.lib.gid_get_preconditioner(self.h)]
 
     def autotune(self, reps: int = 10):
         """Pick the fastest PCG execution (tile rows, 0 = persistent) on the current frame;
