@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start comparison")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the editing, clustering, correction and preconditioner measurements (profiling runs)")
     ap.add_argument("--tile", type=int, default=None, choices=[0, 2, 4, 8, 17],
                     help="operator tile rows instead of autotuning (0 = persistent PCG kernel); for profiling")
     ap.add_argument("--workload", default="video", choices=["video", "batch", "stream"],
@@ -351,7 +353,7 @@ def run_gid(args, ws, rank, local):
     # editing (Sec. 7.4): recombination of the last frame's layers with one recoloured
     # object, one re-keyed and one suppressed indirect layer
     editing = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         bn = s.base_colors().copy()
         bn[0] = bn[0][::-1]
         gains = np.ones(K, np.float32)
@@ -375,7 +377,7 @@ def run_gid(args, ws, rank, local):
 
     # chromaticity clustering of frame 0 (Sec. 4.1), the step before the solve
     clustering = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         for _ in range(3):
             gid.cluster(rgb[0])
         t0 = time.perf_counter()
@@ -387,7 +389,7 @@ def run_gid(args, ws, rank, local):
 
     # misclustering correction (Sec. 4.2) of one region of frame 0: K candidate solves as one batch
     correction = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         region = torch.zeros((H, W), dtype=torch.uint8, device=dev)
         region[H // 4:H // 2, W // 4:W // 2] = (lab[0][H // 4:H // 2, W // 4:W // 2] == int(lab[0][H // 3, W // 3]))
         torch.cuda.synchronize()
@@ -400,7 +402,7 @@ def run_gid(args, ws, rank, local):
     # preconditioners (Sec. 6.1 names none): Jacobi vs per-pixel block-Jacobi on frame 0,
     # cold start, 8 Gauss-Newton steps of M PCG steps; final energy against solve time
     preconditioners = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         preconditioners = []
         sp = gid.Solver(H, W, K, gid.default_weights(off_s))
         sp.set_frame(rgb[0], lab[0])
@@ -429,7 +431,7 @@ def run_gid(args, ws, rank, local):
     # at or below the Jacobi 8 x 20 solve's (energies from untimed passes), then timed
     # like the headline (CUDA events, L2 flushed between steps)
     block_arm = None
-    if rank == 0:
+    if rank == 0 and not args.no_extras:
         def video_energies(solver, Mi):
             solver.new_sequence()
             out = []

@@ -254,8 +254,10 @@ int gid_set_apply_tile(gid_ctx* ctx, int rows);
  * M = diag(J^T J).  GID_PRECOND_BLOCK: M = the per-pixel (K+4) x (K+4) diagonal
  * blocks of J^T J (the unknowns r_R, r_G, r_B, T_0..T_K of one pixel coupled
  * through the data and monochrome terms), factored once per Gauss-Newton step
- * by an FP32 Cholesky per pixel (a pixel whose block rounding made indefinite
- * falls back to its diagonal).  The block form stores (K+4)(K+5)/2 extra planes
+ * in FP32 per pixel (the reflectance part is diagonal: its Schur complement on
+ * the layers is Cholesky-factored; a pixel whose block rounding made
+ * indefinite falls back to its diagonal).  The block form stores
+ * 6 + (K+1)(K+2)/2 extra planes
  * (allocated on the first switch; GID_ERR_OOM if that fails) and always runs
  * one operator and one vector kernel per PCG step (the persistent loop of
  * gid_set_apply_tile(0) is Jacobi only).  Synchronises the context's streams

@@ -59,7 +59,7 @@ struct gid_ctx {
   int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
   int precond = 0;          // GID_PRECOND_JACOBI or GID_PRECOND_BLOCK (gid_set_preconditioner)
-  float* blk = nullptr;     // block-Jacobi factors, V (V + 1) / 2 planes (allocated on first use)
+  float* blk = nullptr;     // block-Jacobi blocks in Schur form, block_planes(K) planes (allocated on first use)
   int blk_blocks = 0;       // grid of the block-Jacobi vector step
   // CUDA graphs of gid_run's launch sequence, replayed on a context-owned stream
   struct Graph {
@@ -1148,7 +1148,7 @@ extern "C" int gid_set_preconditioner(gid_ctx* c, int kind) {
     return fail(c, GID_ERR_INVALID_ARG, "preconditioner must be GID_PRECOND_JACOBI or GID_PRECOND_BLOCK");
   if (kind == c->precond) return GID_OK;
   if (kind == GID_PRECOND_BLOCK && !c->blk) {
-    const size_t nb = (size_t)c->V * (c->V + 1) / 2;
+    const size_t nb = (size_t)block_planes(c->K);
     if (cudaMalloc(&c->blk, nb * c->plane * sizeof(float)) != cudaSuccess) {
       cudaGetLastError();
       c->blk = nullptr;

@@ -76,7 +76,7 @@ struct Params {
   float* q;
   float* Minv;
   float* coef;  // operator coefficient planes written by k_linearize (CoefLayout)
-  float* blk;   // block-Jacobi: packed Cholesky factors, V (V + 1) / 2 planes (k_block_factor)
+  float* blk;   // block-Jacobi blocks in Schur form, block_planes(K) planes (k_block_factor)
   DevColors* col;
   DevScalars* sc;
   double* partial;
@@ -787,23 +787,20 @@ __device__ __forceinline__ void prefetch_l2(const void* p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// The operator tile's compute phase reads every coefficient plane (and p_old,
-// q_old) at the tile's own pixels: start all of those rows towards L2, so that
-// their DRAM latency overlaps the staging instead of the dependent math.  None
-// of them is written by the PCG vector step, so this may run before the grid
-// dependency on it is resolved.
+// The operator tile's compute phase reads every coefficient plane at the
+// tile's own pixels: start those rows towards L2, so that their DRAM latency
+// overlaps the staging instead of the dependent math.  None of them is written
+// by the PCG vector step, so this may run before the grid dependency on it is
+// resolved.  (p_old and q_old, written by the previous operator step, are
+// mostly still in L2: prefetching them too measured 0.4 % slower.)
 template <int K, int TH>
-__device__ __forceinline__ void prefetch_tile(const Params& P, int x0, int y0, int mode, int first, const float* pin,
-                                              const float* qout) {
-  constexpr int V = K + 4, NTH = BX * TH;
-  const int nc = coef_planes(K, P.ns), npl = nc + ((mode == 0 && !first) ? 2 * V : 0);
+__device__ __forceinline__ void prefetch_tile(const Params& P, int x0, int y0) {
+  constexpr int NTH = BX * TH;
+  const int nc = coef_planes(K, P.ns);
   const unsigned bytes = 4u * (unsigned)min(VTW, P.pitch - x0);
-  for (int i = tid_flat(); i < npl * TH; i += NTH) {
+  for (int i = tid_flat(); i < nc * TH; i += NTH) {
     const int pl = i / TH, y = y0 + (i - pl * TH);
-    if (y >= P.H) continue;
-    const float* base = pl < nc ? P.coef + (long)pl * P.plane
-                                : (pl < nc + V ? pin + (long)(pl - nc) * P.plane : qout + (long)(pl - nc - V) * P.plane);
-    prefetch_l2(base + off2(P, y, x0), bytes);
+    if (y < P.H) prefetch_l2(P.coef + (long)pl * P.plane + off2(P, y, x0), bytes);
   }
 }
 
@@ -991,7 +988,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
   ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
-  prefetch_tile<K, TH>(P, blockIdx.x * VTW, blockIdx.y * TH, mode, first, pin, qout);
+  prefetch_tile<K, TH>(P, blockIdx.x * VTW, blockIdx.y * TH);
   // everything below reads what the previous PCG vector step wrote
   grid_dep_wait();
   grid_dep_release();
@@ -1117,17 +1114,13 @@ __global__ void __launch_bounds__(256, 4) k_update(Params P, int it, int nb_prev
 // pixel put entries off its diagonal: the three data rows (r_c with every T_k,
 // T_k with T_l) and the three monochrome rows (T_k with T_l); every other term
 // adds to the diagonal alone.  Variables in plane order r_0..r_2, T_0..T_K;
-// packed lower triangle, entry (i, j), j <= i, at i (i + 1) / 2 + j.
+// a packed lower triangle holds entry (i, j), j <= i, at i (i + 1) / 2 + j.
 __host__ __device__ constexpr int tri(int i, int j) { return i * (i + 1) / 2 + j; }
 
-// In-register Cholesky B = L L^T of a packed SPD block.  A pivot that is not
-// positive (a block that rounding made indefinite) turns the whole block into
-// its diagonal, i.e. that pixel falls back to Jacobi.
+// In-register Cholesky B = L L^T of a packed SPD block; false if a pivot is
+// not positive (a block that rounding made indefinite).
 template <int V>
-__device__ __forceinline__ void block_cholesky(float (&L)[V * (V + 1) / 2]) {
-  float dg[V];
-#pragma unroll
-  for (int i = 0; i < V; i++) dg[i] = L[tri(i, i)];
+__device__ __forceinline__ bool block_cholesky(float (&L)[V * (V + 1) / 2]) {
   bool ok = true;
 #pragma unroll
   for (int j = 0; j < V; j++) {
@@ -1145,12 +1138,7 @@ __device__ __forceinline__ void block_cholesky(float (&L)[V * (V + 1) / 2]) {
       L[tri(i, j)] = t * inv;
     }
   }
-  if (!ok) {
-#pragma unroll
-    for (int i = 0; i < V; i++)
-#pragma unroll
-      for (int j = 0; j <= i; j++) L[tri(i, j)] = i == j ? sqrtf(dg[i]) : 0.f;
-  }
+  return ok;
 }
 
 // y = (L L^T)^-1 r by forward and back substitution (r and y may be one array).
@@ -1186,13 +1174,77 @@ __device__ __forceinline__ float block_norm2(const float (&L)[V * (V + 1) / 2], 
   return s;
 }
 
+// The reflectance part D_r of every block is diagonal (no row couples two
+// reflectance channels of a pixel), and its coupling to the layers is
+// E[c][k] = l_data R_c^2 S_c b_kc = e_c b_kc.  So a block is kept in Schur form:
+//   planes 0..2   1 / D_r,c
+//   planes 3..5   e_c
+//   planes 6..    the packed Cholesky factor of S = B_T - E^T D_r^-1 E
+//                 ((K + 1) x (K + 2) / 2 planes)
+// and B y = q is solved as y_T = S^-1 (q_T - E^T D_r^-1 q_r),
+// y_r = D_r^-1 (q_r - E y_T); z^T B z = sum_c D_r,c (z_rc + (D_r^-1 E z_T)_c)^2
+// + |L_S^T z_T|^2.  6 + (K + 1)(K + 2)/2 planes (34 at K = 6) instead of the
+// full factor's (K + 4)(K + 5)/2 (55).
+__host__ __device__ constexpr int block_planes(int K) { return 6 + (K + 1) * (K + 2) / 2; }
+
+template <int K>
+struct SchurBlock {
+  static constexpr int T = K + 1, NS = T * (T + 1) / 2;
+  float dinv[3], e[3], L[NS];
+};
+
+template <int K>
+__device__ __forceinline__ void schur_solve(const SchurBlock<K>& B, const ColorTable<K>& ct, const float (&q)[K + 4],
+                                            float (&y)[K + 4]) {
+  constexpr int T = K + 1;
+  float t[3], r[T];
+#pragma unroll
+  for (int c = 0; c < 3; c++) t[c] = B.e[c] * B.dinv[c] * q[c];
+#pragma unroll
+  for (int k = 0; k < T; k++) {
+    float v = q[3 + k];
+#pragma unroll
+    for (int c = 0; c < 3; c++) v = fmaf(-ct.b[k][c], t[c], v);
+    r[k] = v;
+  }
+  float yt[T];
+  block_solve<T>(B.L, r, yt);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float ez = 0.f;
+#pragma unroll
+    for (int k = 0; k < T; k++) ez = fmaf(ct.b[k][c], yt[k], ez);
+    y[c] = B.dinv[c] * fmaf(-B.e[c], ez, q[c]);
+  }
+#pragma unroll
+  for (int k = 0; k < T; k++) y[3 + k] = yt[k];
+}
+
+template <int K>
+__device__ __forceinline__ float schur_norm2(const SchurBlock<K>& B, const ColorTable<K>& ct, const float (&z)[K + 4]) {
+  constexpr int T = K + 1;
+  float zt[T];
+#pragma unroll
+  for (int k = 0; k < T; k++) zt[k] = z[3 + k];
+  float s = block_norm2<T>(B.L, zt);
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    float ez = 0.f;
+#pragma unroll
+    for (int k = 0; k < T; k++) ez = fmaf(ct.b[k][c], zt[k], ez);
+    const float w = fmaf(B.dinv[c] * B.e[c], ez, z[c]);
+    s = fmaf(w * w, 1.0f / B.dinv[c], s);
+  }
+  return s;
+}
+
 // Block-Jacobi PCG start, after k_linearize mode 3 (g in z, diag J^T J in Minv):
-// build B(x) from that diagonal and the step's coefficient planes (A_c =
-// l_data R_c^2, S_c, the monochrome weight), factor it, store the factor
+// form the Schur block from that diagonal and the step's coefficient planes
+// (A_c = l_data R_c^2, S_c, the monochrome weight), factor S, store the block
 // (P.blk), z = B^-1 g, rho = <g, z>.
 template <int K>
 __global__ void __launch_bounds__(NT) k_block_factor(Params P) {
-  constexpr int V = K + 4, NB = V * (V + 1) / 2;
+  constexpr int V = K + 4, T = K + 1, NS = T * (T + 1) / 2;
   using CL = CoefLayout<K>;
   __shared__ ColorTable<K> ct;
   load_colors<K>(ct, P.col);
@@ -1201,39 +1253,61 @@ __global__ void __launch_bounds__(NT) k_block_factor(Params P) {
   if (x < P.W && y < P.H) {
     const long o = off2(P, y, x);
     const float* cf = P.coef + o;
-    float A[3], S[3];
+    float A[3], S[3], dg[V], g[V];
 #pragma unroll
     for (int c = 0; c < 3; c++) {
       A[c] = cf[(CL::A + c) * P.plane];
       S[c] = cf[(CL::S + c) * P.plane];
     }
     const float wm = cf[CL::WM * P.plane];
-    float L[NB];
 #pragma unroll
-    for (int i = 0; i < V; i++) L[tri(i, i)] = P.Minv[i * P.plane + o];
-    L[tri(1, 0)] = L[tri(2, 0)] = L[tri(2, 1)] = 0.f;
+    for (int v = 0; v < V; v++) {
+      dg[v] = P.Minv[v * P.plane + o];
+      g[v] = P.z[v * P.plane + o];
+    }
+    SchurBlock<K> B;
+    bool ok = true;
 #pragma unroll
-    for (int k = 0; k <= K; k++) {
+    for (int c = 0; c < 3; c++) {
+      ok = ok && dg[c] > 0.f;
+      B.dinv[c] = 1.0f / dg[c];
+      B.e[c] = A[c] * S[c];
+    }
 #pragma unroll
-      for (int c = 0; c < 3; c++) L[tri(3 + k, c)] = A[c] * S[c] * ct.b[k][c];
+    for (int k = 0; k < T; k++)
 #pragma unroll
-      for (int l = 0; l < k; l++) {
-        float t = 0.f, m = 0.f;
+      for (int l = 0; l <= k; l++) {
+        float bt = 0.f, m = 0.f, ee = 0.f;
 #pragma unroll
         for (int c = 0; c < 3; c++) {
-          t = fmaf(A[c] * ct.b[k][c], ct.b[l][c], t);
+          bt = fmaf(A[c] * ct.b[k][c], ct.b[l][c], bt);
           m = fmaf(ct.dm[k][c], ct.dm[l][c], m);
+          ee = fmaf(B.e[c] * B.e[c] * B.dinv[c] * ct.b[k][c], ct.b[l][c], ee);
         }
-        L[tri(3 + k, 3 + l)] = fmaf(wm, m, t);
+        B.L[tri(k, l)] = (l == k ? dg[3 + k] : fmaf(wm, m, bt)) - ee;
       }
+    ok = ok && block_cholesky<T>(B.L);
+    if (!ok) {  // Jacobi for this pixel
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        B.dinv[c] = 1.0f / dg[c];
+        B.e[c] = 0.f;
+      }
+#pragma unroll
+      for (int k = 0; k < T; k++)
+#pragma unroll
+        for (int l = 0; l <= k; l++) B.L[tri(k, l)] = l == k ? sqrtf(dg[3 + k]) : 0.f;
     }
-    float g[V], z[V];
+    float* blk = P.blk + o;
 #pragma unroll
-    for (int v = 0; v < V; v++) g[v] = P.z[v * P.plane + o];
-    block_cholesky<V>(L);
+    for (int c = 0; c < 3; c++) {
+      blk[c * P.plane] = B.dinv[c];
+      blk[(3 + c) * P.plane] = B.e[c];
+    }
 #pragma unroll
-    for (int j = 0; j < NB; j++) P.blk[j * P.plane + o] = L[j];
-    block_solve<V>(L, g, z);
+    for (int j = 0; j < NS; j++) blk[(6 + j) * P.plane] = B.L[j];
+    float z[V];
+    schur_solve<K>(B, ct, g, z);
 #pragma unroll
     for (int v = 0; v < V; v++) {
       P.z[v * P.plane + o] = z[v];
@@ -1256,15 +1330,20 @@ __global__ void __launch_bounds__(NT) k_block_factor(Params P) {
 
 // Block-Jacobi PCG vector step it: alpha = rho / <p, q>; delta += alpha p,
 // z -= alpha B^-1 q (= B^-1 (r - alpha q); r is not stored), block partials of
-// rho' = <r', z'> = z'^T B z' = |L^T z'|^2.  One pixel per thread, grid-strided
-// over the pitched plane (padding columns skipped: their entries are zero).
-// last 1 / 2 as for k_update (they do not involve the preconditioner).  Each
-// thread holds a whole factor in registers: two blocks per SM up to K = 4, one
-// above (a factor of 55 to 105 floats).
+// rho' = <r', z'> = z'^T B z'.  One pixel per thread, grid-strided over the
+// pitched plane (padding columns skipped: their entries are zero).  last 1 / 2
+// as for k_update (they do not involve the preconditioner).  Every load of a
+// pixel is issued before its first store (a cache-hinted store is ordered
+// before the loads that follow it); each thread then holds the whole block,
+// so above K = 4 the kernel runs one 256-thread block per SM without a
+// register cap (a 128-register cap for two blocks spilled and measured 20 %
+// slower at K = 6).
 template <int K>
 __global__ void __launch_bounds__(256, K <= 4 ? 2 : 1)
     k_update_block(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
-  constexpr int V = K + 4, NB = V * (V + 1) / 2;
+  constexpr int V = K + 4, T = K + 1, NS = T * (T + 1) / 2;
+  __shared__ ColorTable<K> ct;
+  load_colors<K>(ct, P.col);
   grid_dep_wait();  // the operator step's p, q and partials
   grid_dep_release();
   const double pq = block_total(part_share(pcg_partials(P, PART_PQ, it), nb_prev));
@@ -1273,8 +1352,7 @@ __global__ void __launch_bounds__(256, K <= 4 ? 2 : 1)
     update_range<K>(P, p, alpha, last, (long)blockIdx.x * blockDim.x + threadIdx.x, (long)gridDim.x * blockDim.x);
     return;
   }
-  // Distinct planes: every load of a pixel is issued before its first store.
-  // The factors are read once per step and streamed past L2 (evict first), like
+  // The blocks are read once per step and streamed past L2 (evict first), like
   // delta, so that the operator step's planes stay resident.
   const float* __restrict__ blk = P.blk;
   const float* __restrict__ qv = P.q;
@@ -1285,24 +1363,30 @@ __global__ void __launch_bounds__(256, K <= 4 ? 2 : 1)
   const unsigned pitch = (unsigned)P.pitch, W = (unsigned)P.W;
   for (long o = (long)blockIdx.x * blockDim.x + threadIdx.x; o < plane; o += (long)gridDim.x * blockDim.x) {
     if ((unsigned)o % pitch >= W) continue;
-    float L[NB], y[V], pp[V], dd[V], z[V];
+    SchurBlock<K> B;
+    float q[V], y[V], pp[V], dd[V], z[V];
 #pragma unroll
-    for (int j = 0; j < NB; j++) L[j] = __ldcs(blk + j * plane + o);
+    for (int c = 0; c < 3; c++) {
+      B.dinv[c] = __ldcs(blk + c * plane + o);
+      B.e[c] = __ldcs(blk + (3 + c) * plane + o);
+    }
+#pragma unroll
+    for (int jj = 0; jj < NS; jj++) B.L[jj] = __ldcs(blk + (6 + jj) * plane + o);
 #pragma unroll
     for (int v = 0; v < V; v++) {
-      y[v] = qv[v * plane + o];
+      q[v] = qv[v * plane + o];
       pp[v] = p[v * plane + o];
       dd[v] = __ldcs(dv + v * plane + o);
       z[v] = zv[v * plane + o];
     }
-    block_solve<V>(L, y, y);
+    schur_solve<K>(B, ct, q, y);
 #pragma unroll
     for (int v = 0; v < V; v++) {
       z[v] = fmaf(-alpha, y[v], z[v]);
       __stcs(dv + v * plane + o, fmaf(alpha, pp[v], dd[v]));
       zv[v * plane + o] = z[v];
     }
-    rz += block_norm2<V>(L, z);
+    rz += schur_norm2<K>(B, ct, z);
   }
   const double bs = block_sum_f(rz);
   if (threadIdx.x == 0) pcg_partials(P, PART_RZ, it)[blockIdx.x] = bs;
@@ -1368,7 +1452,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     const float beta = first ? 0.f : (rho_old != 0.0 ? (float)(rho / rho_old) : 0.f);
     float pq = 0.f;
     for (int tile = b; tile < ntiles; tile += nb) {
-      prefetch_tile<K, TH>(P, (tile % ntx) * VTW, (tile / ntx) * TH, 0, first, p, q);
+      prefetch_tile<K, TH>(P, (tile % ntx) * VTW, (tile / ntx) * TH);
       pq += apply_tile<K, TH>(P, t, ct, (tile % ntx) * VTW, (tile / ntx) * TH, 0, first, [&]() { return beta; }, p, p,
                               q);
       __syncthreads();  // the next tile re-stages shared memory
