@@ -132,3 +132,65 @@ def test_bad_preconditioner_is_rejected():
     with pytest.raises(gid.GidError):
         s._chk(s.lib.gid_set_preconditioner(s.h, 7))
     assert s.preconditioner() == "jacobi"
+
+
+@pytest.mark.slow
+def test_block_jacobi_full_size_640x480_K6():
+    """The 640 x 480 K = 6 frame in the launch configuration the benchmark times
+    (128 x 17 operator tile): 20 block-Jacobi PCG steps from the cold start
+    against the oracle's, then one outer iteration end to end."""
+    case = Case(H=480, W=640, K=6, n_cells=40, seed=0)
+    s = case.solver()
+    s.set_preconditioner("block")
+    s.set_apply_tile(17)
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    s.init(0)
+    X = s.state().cpu().numpy().astype(np.float64)
+    pb = case.oracle_problem()
+    delta = s.stage_pcg(20).cpu().numpy()
+    ref, _ = pb.pcg_variant(X, 20, block=True)
+    err = np.abs(delta - ref).max()
+    assert err <= 1e-4 * np.abs(ref).max(), f"max err {err:.3e} vs {np.abs(ref).max():.3e}"
+    s.run(1, 20)
+    R, T = s.layers()
+    E, _ = s.energy()
+    Xo, bo, hist = O.solve_frame(pb, X, 1, 20, block=True)
+    assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
+    assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
+    assert np.abs(s.base_colors() - bo).max() <= 1e-3
+    assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+def test_batch_uses_each_contexts_preconditioner():
+    """Contexts of a batch set to block-Jacobi before its first run give, bit for
+    bit, what the same videos give solved one context at a time."""
+    from paper_1908_01961_b300 import gid
+    shapes = [dict(H=48, W=64, K=4, n_cells=12), dict(H=41, W=70, K=6, n_cells=9)]
+    cs = [Case(**sh, seed=20 + i, frames=2, temporal=True) for i, sh in enumerate(shapes)]
+    single = []
+    for c in cs:
+        s = c.solver()
+        s.set_preconditioner("block")
+        s.set_apply_tile(8)
+        for t in range(2):
+            rgb, lab = c.gpu_inputs(t)
+            s.set_frame(rgb, lab)
+            s.init(0 if t == 0 else 1)
+            s.run(3, 6)
+        single.append((s.state().cpu().numpy(), s.base_colors()))
+    weights = [gid.default_weights(c.off_s, c.off_t, temporal=1) for c in cs]
+    b = gid.Batch([(c.H, c.W, c.K) for c in cs], weights)
+    for v, c in zip(b.videos, cs):
+        v.set_base_colors(c.b_init)
+        v.set_apply_tile(8)
+        v.set_preconditioner("block")
+    for t in range(2):
+        ins = [c.gpu_inputs(t) for c in cs]
+        b.set_frames([i[0] for i in ins], [i[1] for i in ins])
+        b.init(0 if t == 0 else 1)
+        b.run(3, 6)
+    for v, (X, bc) in zip(b.videos, single):
+        assert v.preconditioner() == "block"
+        assert np.array_equal(v.state().cpu().numpy(), X)
+        assert np.array_equal(v.base_colors(), bc)
