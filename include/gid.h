@@ -247,6 +247,21 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
  * agree to FP32 rounding order; only speed differs. */
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
+/* ---- fault injection (tests) ---- */
+
+/* Host-side fault injection for failure-detection tests (the paper has no
+ * counterpart).  phantom_blocks > 0 adds that many participants that never
+ * arrive to every grid barrier of the persistent PCG kernel
+ * (gid_set_apply_tile(0)), so every block's bounded wait runs out; spin_limit
+ * > 0 replaces the barrier's poll limit (default 2^22 polls of about 64 ns),
+ * so that the wait gives up after spin_limit polls.  A barrier that gives up
+ * records a status bit and its kernel returns without updating the state; the
+ * next synchronising call returns GID_ERR_TIMEOUT and clears the bit, and the
+ * context stays usable.  gid_debug_inject(ctx, 0, 0) restores the defaults
+ * (a new context starts with them).  Negative arguments: GID_ERR_INVALID_ARG.
+ * Synchronises. */
+int gid_debug_inject(gid_ctx* ctx, int phantom_blocks, long long spin_limit);
+
 /* ---- preconditioner ---- */
 
 /* Sec. 6.1 solves each Gauss-Newton system by preconditioned conjugate

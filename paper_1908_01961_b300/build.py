@@ -14,7 +14,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libgid.so")
 SOURCES = ["gid.cu", "gid_noalloc.cu", "gid_net.cu", "gid_cluster.cu"]
-HEADERS = ["gid_kernels.cuh", "gid_net_kernels.cuh", "gid_net_internal.h"]
+HEADERS = ["gid_kernels.cuh", "gid_net_kernels.cuh", "gid_net_internal.h", "gid_nvtx.h"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-shared", "--expt-relaxed-constexpr"]

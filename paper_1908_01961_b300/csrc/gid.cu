@@ -18,6 +18,7 @@
 #include "../../include/gid.h"
 #include "gid_kernels.cuh"
 #include "gid_net_internal.h"
+#include "gid_nvtx.h"
 
 using namespace gid;
 
@@ -657,6 +658,7 @@ extern "C" int gid_get_base_colors(gid_ctx* c, float* b_host) {
 }
 
 extern "C" int gid_set_frame(gid_ctx* c, const float* rgb_dev, const uint8_t* labels_dev) {
+  gid::NvtxRange nvtx_range("gid_set_frame");
   if (!c || !rgb_dev || !labels_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
   const bool temporal = c->w.temporal && c->w.n_temporal_pairs > 0 && c->frames_solved > 0;
   if (temporal) {
@@ -691,6 +693,7 @@ extern "C" int gid_new_sequence(gid_ctx* c) {
 }
 
 extern "C" int gid_init(gid_ctx* c, int mode) {
+  gid::NvtxRange nvtx_range("gid_init");
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (!c->has_frame || !c->has_colors)
     return fail(c, GID_ERR_STATE, "gid_init needs gid_set_base_colors and gid_set_frame");
@@ -714,6 +717,7 @@ extern "C" int gid_base_color_step(gid_ctx* c) {
 }
 
 extern "C" int gid_init_learned(gid_ctx* c, gid_net* net, float zero_below) {
+  gid::NvtxRange nvtx_range("gid_init_learned");
   if (!c || !net) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
   if (!(zero_below >= 0.f) || !std::isfinite(zero_below)) return fail(c, GID_ERR_INVALID_ARG, "zero_below >= 0");
   if (!c->has_frame || !c->has_colors)
@@ -843,6 +847,7 @@ static int run_graph(gid_ctx* c, int n_outer, int m_inner, bool refine) {
 }
 
 extern "C" int gid_run(gid_ctx* c, int n_outer, int m_inner) {
+  gid::NvtxRange nvtx_range("gid_run");
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (n_outer < 0 || m_inner < 1) return fail(c, GID_ERR_INVALID_ARG, "n_outer >= 0 and m_inner >= 1");
   if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "gid_run before gid_set_frame / gid_init");
@@ -904,11 +909,15 @@ extern "C" int gid_set_state(gid_ctx* c, const float* X_dev) {
   if (!c || !X_dev) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
   GID_TRY_CUDA(c, cudaMemcpy2DAsync(c->X, sizeof(float) * c->pitch, X_dev, sizeof(float) * c->W, sizeof(float) * c->W,
                                     (size_t)c->V * c->H, cudaMemcpyDeviceToDevice, c->stream));
+  if (c->pitch > c->W)  // padding columns are zero (a failed earlier solve may have left NaN there)
+    GID_TRY_CUDA(c, cudaMemset2DAsync(c->X + c->W, sizeof(float) * c->pitch, 0, sizeof(float) * (c->pitch - c->W),
+                                      (size_t)c->V * c->H, c->stream));
   c->initialised = true;
   return GID_OK;
 }
 
 extern "C" int gid_energy_region(gid_ctx* c, const uint8_t* mask_dev, double* total, double* per_term) {
+  gid::NvtxRange nvtx_range("gid_energy");
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (!c->has_frame || !c->initialised) return fail(c, GID_ERR_STATE, "no frame/state");
   launch(c, GID_KIND_ENERGY, [&] { GID_DISPATCH(c, energy, c, mask_dev); });
@@ -931,6 +940,7 @@ extern "C" int gid_energy(gid_ctx* c, double* total, double* per_term) {
 
 extern "C" int gid_solve_frame_host(gid_ctx* c, const float* rgb_host, const uint8_t* labels_host, int init_mode,
                                     int n_outer, int m_inner, float* R_host, float* T_host, float* b_host) {
+  gid::NvtxRange nvtx_range("gid_solve_frame_host");
   if (!c || !rgb_host || !labels_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
   const size_t HW = (size_t)c->H * c->W;
   if (!c->st_rgb) {
@@ -959,6 +969,7 @@ extern "C" int gid_solve_frame_host(gid_ctx* c, const float* rgb_host, const uin
 extern "C" int gid_solve_video_host(gid_ctx* c, int n, const float* rgb_host, const uint8_t* labels_host,
                                     int first_init_mode, int n_outer, int m_inner, float* R_host, float* T_host,
                                     float* b_host) {
+  gid::NvtxRange nvtx_range("gid_solve_video_host");
   if (!c || !rgb_host || !labels_host) return fail(c, GID_ERR_INVALID_ARG, "NULL argument");
   if (n < 1) return fail(c, GID_ERR_INVALID_ARG, "n >= 1 frames");
   if (first_init_mode != 0 && first_init_mode != 1) return fail(c, GID_ERR_INVALID_ARG, "init mode 0 or 1");
@@ -1137,6 +1148,22 @@ extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
     return fail(c, GID_ERR_INVALID_ARG, "tile rows must be 0 (persistent), 2, 4, 8 or 17");
   c->apply_th = rows;
   c->persistent = false;
+  return GID_OK;
+}
+
+// ---------------------------------------------------------------- fault injection (tests)
+
+extern "C" int gid_debug_inject(gid_ctx* c, int phantom_blocks, long long spin_limit) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (phantom_blocks < 0 || spin_limit < 0) return fail(c, GID_ERR_INVALID_ARG, "phantom_blocks, spin_limit >= 0");
+  struct {
+    unsigned int phantom;
+    long long spin_limit;
+  } v = {(unsigned int)phantom_blocks, spin_limit};
+  GID_TRY_CUDA(c, cudaMemcpyAsync(&c->sc->phantom, &v.phantom, sizeof(v.phantom), cudaMemcpyHostToDevice, c->stream));
+  GID_TRY_CUDA(c, cudaMemcpyAsync(&c->sc->spin_limit, &v.spin_limit, sizeof(v.spin_limit), cudaMemcpyHostToDevice,
+                                  c->stream));
+  GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
   return GID_OK;
 }
 
@@ -1382,6 +1409,7 @@ extern "C" int gid_batch_new_sequence(gid_batch* b) {
 // and joined to the batch stream, so the whole frame-step of all videos is one
 // graph launch and the videos' kernels run concurrently.
 extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
+  gid::NvtxRange nvtx_range("gid_batch_run");
   if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
   if (n_outer < 1 || m_inner < 1) return bfail(b, GID_ERR_INVALID_ARG, "n_outer >= 1 and m_inner >= 1");
   std::string key = std::to_string(n_outer) + "," + std::to_string(m_inner);
@@ -1496,6 +1524,7 @@ extern "C" int gid_correct_region(int H, int W, int K, const gid_weights* w, con
                                   const uint8_t* labels_dev, const float* b_init_host, const uint8_t* region_dev,
                                   int n_outer, int m_inner, void* stream, int* best_out, double* sparsity_out,
                                   uint8_t* labels_out_dev) {
+  gid::NvtxRange nvtx_range("gid_correct_region");
   if (!rgb_dev || !labels_dev || !b_init_host || !region_dev || !best_out)
     return fail(nullptr, GID_ERR_INVALID_ARG, "NULL argument");
   if (K < 1 || K > GID_MAX_K || H < 1 || W < 1) return fail(nullptr, GID_ERR_INVALID_ARG, "bad H, W or K");

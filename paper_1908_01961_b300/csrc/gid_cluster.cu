@@ -20,6 +20,7 @@
 #include <vector>
 
 #include "../../include/gid.h"
+#include "gid_nvtx.h"
 
 namespace gidcl {
 
@@ -267,6 +268,7 @@ static int cl_fail(char* errbuf, int errbuf_len, int code, const std::string& m)
 
 extern "C" int gid_cluster(int H, int W, const float* rgb_dev, int k_max, float merge_dist, void* stream,
                            uint8_t* labels_dev, float* b_host, int* k_out, char* errbuf, int errbuf_len) {
+  gid::NvtxRange nvtx_range("gid_cluster");
   if (!rgb_dev || !labels_dev || !b_host || !k_out)
     return cl_fail(errbuf, errbuf_len, GID_ERR_INVALID_ARG, "NULL argument");
   if (H < 1 || W < 1 || (long)H * W > (1L << 28)) return cl_fail(errbuf, errbuf_len, GID_ERR_INVALID_ARG, "bad H, W");

@@ -51,6 +51,11 @@ struct DevScalars {
   double g[3 * GID_MAX_K];
   unsigned int cnt[8];
   int status;
+  // host-side fault injection (gid_debug_inject; zero = off): participants of
+  // the persistent kernel's grid barrier that never arrive, and the barrier's
+  // poll limit (0 = GRID_SPINS)
+  unsigned int phantom;
+  long long spin_limit;
 };
 // arrival counters: linearisation, base-colour step per colour channel (3),
 // energy, persistent-kernel grid barrier (count, generation)
@@ -445,8 +450,13 @@ __global__ void k_reset_colors(DevColors* col, int n) {
 template <int K>
 __global__ void k_init_cold(Params P) {
   const int x = blockIdx.x * BX + threadIdx.x, y = blockIdx.y * BY + threadIdx.y;
-  if (x >= P.W || y >= P.H) return;
+  if (y >= P.H || x >= P.pitch) return;
   const long o = off2(P, y, x);
+  if (x >= P.W) {  // padding columns are zero (a failed earlier solve may have left NaN there)
+#pragma unroll
+    for (int v = 0; v < K + 4; v++) P.X[v * P.plane + o] = 0.f;
+    return;
+  }
   const int l = P.lab[o];
   const float* bsrc = P.w.rcluster_follows_b ? P.col->b : P.col->binit;
   float mi = 0.f, mr = 0.f;
@@ -542,6 +552,12 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
   const Weights& w = P.w;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   float rz = 0.f;
+  if ((mode == 0 || mode == 3) && x >= P.W && x < P.pitch && y < P.H) {
+    // the PCG vectors' padding columns restart at zero every Gauss-Newton step
+    const long o = off2(P, y, x);
+#pragma unroll
+    for (int v = 0; v < V; v++) P.z[v * P.plane + o] = P.d[v * P.plane + o] = P.Minv[v * P.plane + o] = 0.f;
+  }
   if (x < P.W && y < P.H) {
     const Pix px = make_pix(P, x, y);
     const long o = off2(P, y, x), oq = off2(Q, y, x);
@@ -880,6 +896,10 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
     // q = A s on the valid pixels; in a PCG step p = z + beta p_old and, A being
     // fixed within the Gauss-Newton step, q = A p = A z + beta q_old.
     const F4 bb = f4s(beta);
+    // Lanes past the frame's right edge: their coefficients are zero and the
+    // staged tile reads zero outside the frame, so q and p stay zero there (the
+    // first step of every Gauss-Newton step rewrites them from z, whose padding
+    // k_linearize has just zeroed).
     auto finish = [&](int v, F4 s, F4 as) {
       F4 q = mul4(as, valid), p = s;
       const long ov = v * PL + o;
@@ -1397,8 +1417,9 @@ __global__ void __launch_bounds__(256, K <= 4 ? 2 : 1)
 // Grid-wide barrier of a cooperative launch (all blocks co-resident).  Thread 0
 // of each block arrives on a counter; the last to arrive resets it and bumps a
 // generation word the others wait on.  Every wait is bounded: after GRID_SPINS
-// polls the block records ST_TIMEOUT and the barrier returns false, and the
-// kernel then returns (so it always terminates).
+// polls (or the injected limit) the block records ST_TIMEOUT and the barrier
+// returns false, and the kernel then returns (so it always terminates).  An
+// injected phantom participant makes every block's wait run out.
 constexpr long GRID_SPINS = 1L << 22;
 
 __device__ __forceinline__ bool grid_sync(DevScalars* sc) {
@@ -1408,15 +1429,16 @@ __device__ __forceinline__ bool grid_sync(DevScalars* sc) {
     volatile unsigned int* gen = &sc->cnt[CNT_GEN];
     const unsigned int g = *gen;
     __threadfence();
-    const unsigned int n = gridDim.x * gridDim.y;
+    const unsigned int n = gridDim.x * gridDim.y + sc->phantom;
+    const long long limit = sc->spin_limit > 0 ? sc->spin_limit : GRID_SPINS;
     if (atomicAdd(&sc->cnt[CNT_GRID], 1u) == n - 1) {
       sc->cnt[CNT_GRID] = 0u;
       __threadfence();
       atomicAdd(&sc->cnt[CNT_GEN], 1u);
       ok = 1;
     } else {
-      long spins = 0;
-      while (*gen == g && spins < GRID_SPINS) {
+      long long spins = 0;
+      while (*gen == g && spins < limit) {
         __nanosleep(64);
         spins++;
       }

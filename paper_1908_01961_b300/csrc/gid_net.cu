@@ -13,6 +13,7 @@
 #include "../../include/gid.h"
 #include "gid_net_internal.h"
 #include "gid_net_kernels.cuh"
+#include "gid_nvtx.h"
 
 using namespace gidnet;
 
@@ -563,6 +564,7 @@ static void pack_input(gid_net* n, const float* rgb, Planes rg, const uint8_t* l
 
 extern "C" int gid_net_forward(gid_net* n, int B, int H, int W, const float* rgb_dev, const uint8_t* labels_dev,
                                const float* palette_dev, float* r_dev, float* T_dev) {
+  gid::NvtxRange nvtx_range("gid_net_forward");
   if (!n || !rgb_dev || !labels_dev || !palette_dev) return nfail(n, GID_ERR_INVALID_ARG, "NULL argument");
   if (int rc = check_dims(n, B, H, W)) return rc;
   n->s = n->stream;
@@ -580,6 +582,7 @@ extern "C" int gid_net_forward(gid_net* n, int B, int H, int W, const float* rgb
 extern "C" int gid_net_backward(gid_net* n, int B, int H, int W, const float* rgb_dev, const uint8_t* labels_dev,
                                 const float* palette_dev, const float* r_target_dev, const float* T_target_dev,
                                 double* loss_host) {
+  gid::NvtxRange nvtx_range("gid_net_backward");
   if (!n || !rgb_dev || !labels_dev || !palette_dev || !r_target_dev || !T_target_dev)
     return nfail(n, GID_ERR_INVALID_ARG, "NULL argument");
   if (int rc = check_dims(n, B, H, W)) return rc;

@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgid.so")
 
 GID_OK = 0
 PRECOND_JACOBI, PRECOND_BLOCK = 0, 1
+ERR_TIMEOUT, ERR_NUMERIC = -5, -6
 ERRORS = {-1: "GID_ERR_INVALID_ARG", -2: "GID_ERR_CUDA", -3: "GID_ERR_OOM", -4: "GID_ERR_STATE",
           -5: "GID_ERR_TIMEOUT", -6: "GID_ERR_NUMERIC"}
 MAX_K = 10
@@ -31,7 +32,7 @@ EXPORTS = (
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
-    "gid_set_preconditioner", "gid_get_preconditioner",
+    "gid_set_preconditioner", "gid_get_preconditioner", "gid_debug_inject",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
     "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
@@ -100,6 +101,7 @@ def load():
     L.gid_profile_read.argtypes = [P, D, LL]
     L.gid_set_apply_tile.argtypes = [P, I]
     L.gid_set_preconditioner.argtypes = [P, I]
+    L.gid_debug_inject.argtypes = [P, I, ctypes.c_longlong]
     L.gid_get_preconditioner.argtypes = [P]
     L.gid_set_graphs.argtypes = [P, I]
     L.gid_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), F]
@@ -405,6 +407,29 @@ class Solver:
     # -- operator tile shape
     def set_apply_tile(self, rows: int):
         self._chk(self.lib.gid_set_apply_tile(self.h, rows))
+
+    def debug_inject(self, phantom_blocks: int = 0, spin_limit: int = 0):
+        """Fault injection for tests (gid_debug_inject): grid-barrier participants
+        that never arrive and the barrier's poll limit; (0, 0) restores the defaults."""
+        self._chk(self.lib.gid_debug_inject(self.h, phantom_blocks, spin_limit))
+
+    def run_checked(self, n_outer: int, m_inner: int):
+        """gid_run, then the exact energy; if the solve failed numerically
+        (GID_ERR_NUMERIC: non-finite energy or a singular base-colour system) or
+        a device wait gave up (GID_ERR_TIMEOUT), the layers are rolled back to
+        the state before the call (a copy kept here) and the error is raised.
+        The base colours need no copy: a base-colour step whose system is not
+        positive definite (NaN included) leaves them unchanged.  Returns the
+        energy (total, per term)."""
+        X0 = self.state().clone()
+        try:
+            self.run(n_outer, m_inner)
+            return self.energy()
+        except GidError as e:
+            if e.code not in (ERR_NUMERIC, ERR_TIMEOUT):
+                raise
+            self.set_state(X0)
+            raise
 
     def set_preconditioner(self, kind: str):
         """'jacobi' (default) or 'block' (per-pixel diagonal blocks of J^T J)."""
