@@ -247,6 +247,17 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
  * agree to FP32 rounding order; only speed differs. */
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
+/* ---- PCG history ---- */
+
+/* rho_m = <r_m, z_m> (residual against preconditioned residual, Sec. 6.1's
+ * PCG) of the latest Gauss-Newton step that ran, for m = 0 .. n-1 with
+ * n = min(its PCG steps, 64, max_n) written to *n_out (rho_0 at the start;
+ * the last step's final rho is not formed).  FP64 totals of the same block
+ * partials the solver uses for alpha and beta.  rho_host: host array of at
+ * least max_n doubles.  Synchronises, and reports any error a device step
+ * recorded since the last synchronising call. */
+int gid_pcg_history(gid_ctx* ctx, double* rho_host, int max_n, int* n_out);
+
 /* ---- fault injection (tests) ---- */
 
 /* Host-side fault injection for failure-detection tests (the paper has no

@@ -59,6 +59,7 @@ struct gid_ctx {
   int upd_cap = 148 * 4;   // vector-step blocks resident at once (SMs x blocks per SM)
   int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
+  int last_m_inner = 0;    // PCG steps of the latest Gauss-Newton step (gid_pcg_history)
   int precond = 0;          // GID_PRECOND_JACOBI or GID_PRECOND_BLOCK (gid_set_preconditioner)
   float* blk = nullptr;     // block-Jacobi blocks in Schur form, block_planes(K) planes (allocated on first use)
   int blk_blocks = 0;       // grid of the block-Jacobi vector step
@@ -746,6 +747,7 @@ extern "C" int gid_init_learned(gid_ctx* c, gid_net* net, float zero_below) {
 }
 
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
+  c->last_m_inner = m_inner;
   if (c->precond == GID_PRECOND_BLOCK) {
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 3, (float*)nullptr, (float*)nullptr); });
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, block_factor, c); });
@@ -1149,6 +1151,17 @@ extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
   c->apply_th = rows;
   c->persistent = false;
   return GID_OK;
+}
+
+// ---------------------------------------------------------------- PCG history
+
+extern "C" int gid_pcg_history(gid_ctx* c, double* rho_host, int max_n, int* n_out) {
+  if (!c || !rho_host || !n_out || max_n < 0) return fail(c, GID_ERR_INVALID_ARG, "bad argument");
+  const int n = std::min({c->last_m_inner, PCG_HIST, max_n});
+  *n_out = n;
+  if (n > 0)
+    GID_TRY_CUDA(c, cudaMemcpyAsync(rho_host, c->sc->rho_hist, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));
+  return sync_status(c);
 }
 
 // ---------------------------------------------------------------- fault injection (tests)

@@ -56,7 +56,10 @@ struct DevScalars {
   // poll limit (0 = GRID_SPINS)
   unsigned int phantom;
   long long spin_limit;
+  // rho_m = <r_m, z_m> of the latest Gauss-Newton step, m = 0 .. min(M, PCG_HIST) - 1
+  double rho_hist[64];
 };
+constexpr int PCG_HIST = 64;
 // arrival counters: linearisation, base-colour step per colour channel (3),
 // energy, persistent-kernel grid barrier (count, generation)
 enum { CNT_LIN, CNT_DENSE, CNT_ENERGY = CNT_DENSE + 3, CNT_GRID, CNT_GEN };
@@ -706,6 +709,7 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
     if (tid_flat() == 0) {
       P.sc->rho = t;
       P.sc->rho2[1] = t;  // rho of PCG step 1
+      P.sc->rho_hist[0] = t;
       P.sc->beta = 0.0;
       P.sc->cnt[CNT_GRID] = 0u;  // arrival counter of the persistent PCG kernel's grid barrier
     }
@@ -1019,7 +1023,10 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
   auto get_beta = [&]() -> float {
     if (!use_beta) return 0.f;
     const double rho = block_total(rho_share), rho_old = P.sc->rho2[(it - 1) & 1];
-    if (tid_flat() == 0 && blockIdx.x == 0 && blockIdx.y == 0) P.sc->rho2[it & 1] = rho;
+    if (tid_flat() == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+      P.sc->rho2[it & 1] = rho;
+      if (it - 1 < PCG_HIST) P.sc->rho_hist[it - 1] = rho;
+    }
     return rho_old != 0.0 ? (float)(rho / rho_old) : 0.f;
   };
   const float pq = apply_tile<K, TH>(P, t, ct, blockIdx.x * VTW, blockIdx.y * TH, mode, first, get_beta, pin, pout, qout,
@@ -1342,6 +1349,7 @@ __global__ void __launch_bounds__(NT) k_block_factor(Params P) {
     if (tid_flat() == 0) {
       P.sc->rho = t;
       P.sc->rho2[1] = t;  // rho of PCG step 1
+      P.sc->rho_hist[0] = t;
       P.sc->beta = 0.0;
       P.sc->cnt[CNT_GRID] = 0u;
     }
@@ -1493,6 +1501,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     if (!grid_sync(P.sc)) return;
     rho_old = rho;
     rho = block_total(part_share(part_rz, nb));
+    if (b == 0 && tid == 0 && m < PCG_HIST) P.sc->rho_hist[m] = rho;
   }
 }
 
