@@ -17,7 +17,9 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 
-@pytest.mark.parametrize("H,W,K,n_cells,seed", [(48, 64, 4, 12, 0), (120, 160, 6, 20, 3), (37, 29, 3, 7, 1)])
+# the last case is the 640 x 480 K = 6 frame the benchmark clusters
+@pytest.mark.parametrize("H,W,K,n_cells,seed", [(48, 64, 4, 12, 0), (120, 160, 6, 20, 3), (37, 29, 3, 7, 1),
+                                                (480, 640, 6, 40, 0)])
 def test_cluster_matches_oracle(H, W, K, n_cells, seed):
     from paper_1908_01961_b300 import gid
     f = synth.SyntheticVideo(H, W, K, n_cells, seed=seed).frame(0)

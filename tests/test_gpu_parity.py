@@ -332,3 +332,24 @@ def test_recombine_matches_oracle():
     close(out.cpu().numpy(), ref, 1e-5, "recombined image")
     same = s.recombine()                                  # b and unit gains: the model's reconstruction
     close(same.cpu().numpy(), O.recombine(X, b, b, np.ones(6), np.zeros_like(mask)), 1e-5, "reconstruction")
+
+
+def test_recombine_full_size_640x480_K6():
+    """The benchmark's editing call at its size: a 640 x 480 K = 6 state, one
+    recoloured object, one suppressed layer, against the oracle's recombination."""
+    case = Case(H=480, W=640, K=6, n_cells=40, seed=0)
+    s = case.solver()
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    s.init(0)
+    s.run(1, 4)
+    X = s.state().cpu().numpy().astype(np.float64)
+    b = s.base_colors().astype(np.float64)
+    bn = b.astype(np.float32).copy()
+    bn[0] = bn[0][::-1]
+    g = np.ones(6, np.float32)
+    g[1] = 0.0
+    mask = np.where(case.frames[0].labels == 2, 3, 0).astype(np.uint8)
+    out = s.recombine(bn, g, torch.from_numpy(mask).cuda())
+    ref = O.recombine(X, b, bn.astype(np.float64), g.astype(np.float64), mask)
+    close(out.cpu().numpy(), ref, 1e-5, "recombined image")
