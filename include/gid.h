@@ -249,13 +249,21 @@ int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
 /* ---- PCG history ---- */
 
+/* Recording of the PCG history, off by default: when on, each PCG step's rho
+ * is copied into a device-side history by one 8-byte device copy after its
+ * operator step (the kernels themselves are unchanged, so the default path
+ * pays nothing for it).  The persistent PCG kernel (gid_set_apply_tile(0),
+ * Jacobi) always records.  Changing it synchronises the context's streams and
+ * drops its cached graphs. */
+int gid_set_pcg_history(gid_ctx* ctx, int on);
+
 /* rho_m = <r_m, z_m> (residual against preconditioned residual, Sec. 6.1's
  * PCG) of the latest Gauss-Newton step that ran, for m = 0 .. n-1 with
  * n = min(its PCG steps, 64, max_n) written to *n_out (rho_0 at the start;
- * the last step's final rho is not formed).  FP64 totals of the same block
- * partials the solver uses for alpha and beta.  rho_host: host array of at
- * least max_n doubles.  Synchronises, and reports any error a device step
- * recorded since the last synchronising call. */
+ * the last step's final rho is not formed); n = 0 if that step did not record.
+ * FP64 totals of the same block partials the solver uses for alpha and beta.
+ * rho_host: host array of at least max_n doubles.  Synchronises, and reports
+ * any error a device step recorded since the last synchronising call. */
 int gid_pcg_history(gid_ctx* ctx, double* rho_host, int max_n, int* n_out);
 
 /* ---- fault injection (tests) ---- */

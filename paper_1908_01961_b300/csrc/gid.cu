@@ -60,6 +60,8 @@ struct gid_ctx {
   int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
   int last_m_inner = 0;    // PCG steps of the latest Gauss-Newton step (gid_pcg_history)
+  bool record_rho = false;  // copy each PCG step's rho into the history (gid_set_pcg_history)
+  bool hist_valid = false;  // the latest Gauss-Newton step recorded its history
   int precond = 0;          // GID_PRECOND_JACOBI or GID_PRECOND_BLOCK (gid_set_preconditioner)
   float* blk = nullptr;     // block-Jacobi blocks in Schur form, block_planes(K) planes (allocated on first use)
   int blk_blocks = 0;       // grid of the block-Jacobi vector step
@@ -746,8 +748,17 @@ extern "C" int gid_init_learned(gid_ctx* c, gid_net* net, float zero_below) {
   return GID_OK;
 }
 
+// With recording on: rho of PCG step m (published in rho2 by the operator step
+// m, or by the PCG start for m = 1) into the history; an 8-byte device copy
+// in the stream, so the kernels themselves carry nothing for it.
+static void record_rho(gid_ctx* c, int m) {
+  if (c->record_rho && m >= 2 && m - 1 < PCG_HIST)
+    cudaMemcpyAsync(&c->sc->rho_hist[m - 1], &c->sc->rho2[m & 1], sizeof(double), cudaMemcpyDeviceToDevice, c->stream);
+}
+
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   c->last_m_inner = m_inner;
+  c->hist_valid = c->record_rho || (c->persistent && c->pcg_blocks > 0 && c->precond == GID_PRECOND_JACOBI);
   if (c->precond == GID_PRECOND_BLOCK) {
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 3, (float*)nullptr, (float*)nullptr); });
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, block_factor, c); });
@@ -755,6 +766,7 @@ static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
     for (int m = 1; m <= m_inner; m++) {
       launch(c, GID_KIND_APPLY,
              [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, m, (const float*)c->pA, c->pA, c->q); });
+      record_rho(c, m);
       launch(c, GID_KIND_UPDATE,
              [&] { GID_DISPATCH(c, update_block, c, m, (const float*)c->pA, m == m_inner ? last_mode : 0); });
     }
@@ -785,6 +797,7 @@ static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   for (int m = 1; m <= m_inner; m++) {
     launch(c, GID_KIND_APPLY,
            [&] { GID_DISPATCH(c, apply, c, 0, m == 1 ? 1 : 0, m, (const float*)c->pA, c->pA, c->q); });
+    record_rho(c, m);
     launch(c, GID_KIND_UPDATE, [&] { GID_DISPATCH(c, update, c, m, (const float*)c->pA, m == m_inner ? last_mode : 0); });
   }
   return check_launch(c, "pcg");
@@ -1155,9 +1168,21 @@ extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
 
 // ---------------------------------------------------------------- PCG history
 
+extern "C" int gid_set_pcg_history(gid_ctx* c, int on) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if ((on != 0) == c->record_rho) return GID_OK;
+  // the cached graphs hold the other launch sequence
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->gs) cudaStreamSynchronize(c->gs);
+  for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+  c->graphs.clear();
+  c->record_rho = on != 0;
+  return GID_OK;
+}
+
 extern "C" int gid_pcg_history(gid_ctx* c, double* rho_host, int max_n, int* n_out) {
   if (!c || !rho_host || !n_out || max_n < 0) return fail(c, GID_ERR_INVALID_ARG, "bad argument");
-  const int n = std::min({c->last_m_inner, PCG_HIST, max_n});
+  const int n = c->hist_valid ? std::min({c->last_m_inner, PCG_HIST, max_n}) : 0;
   *n_out = n;
   if (n > 0)
     GID_TRY_CUDA(c, cudaMemcpyAsync(rho_host, c->sc->rho_hist, sizeof(double) * n, cudaMemcpyDeviceToHost, c->stream));

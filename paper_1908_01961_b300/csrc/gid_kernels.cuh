@@ -57,6 +57,7 @@ struct DevScalars {
   unsigned int phantom;
   long long spin_limit;
   // rho_m = <r_m, z_m> of the latest Gauss-Newton step, m = 0 .. min(M, PCG_HIST) - 1
+  // (slot 0 by the PCG start; the others copied from rho2 when recording is on)
   double rho_hist[64];
 };
 constexpr int PCG_HIST = 64;
@@ -1023,10 +1024,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
   auto get_beta = [&]() -> float {
     if (!use_beta) return 0.f;
     const double rho = block_total(rho_share), rho_old = P.sc->rho2[(it - 1) & 1];
-    if (tid_flat() == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
-      P.sc->rho2[it & 1] = rho;
-      if (it - 1 < PCG_HIST) P.sc->rho_hist[it - 1] = rho;
-    }
+    if (tid_flat() == 0 && blockIdx.x == 0 && blockIdx.y == 0) P.sc->rho2[it & 1] = rho;
     return rho_old != 0.0 ? (float)(rho / rho_old) : 0.f;
   };
   const float pq = apply_tile<K, TH>(P, t, ct, blockIdx.x * VTW, blockIdx.y * TH, mode, first, get_beta, pin, pout, qout,

@@ -35,6 +35,7 @@ EXPORTS = (
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
     "gid_set_preconditioner", "gid_get_preconditioner", "gid_debug_inject", "gid_pcg_history",
+    "gid_set_pcg_history",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
     "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
@@ -105,6 +106,7 @@ def load():
     L.gid_set_preconditioner.argtypes = [P, I]
     L.gid_debug_inject.argtypes = [P, I, ctypes.c_longlong]
     L.gid_pcg_history.argtypes = [P, D, I, ctypes.POINTER(I)]
+    L.gid_set_pcg_history.argtypes = [P, I]
     L.gid_get_preconditioner.argtypes = [P]
     L.gid_set_graphs.argtypes = [P, I]
     L.gid_autotune.argtypes = [P, I, ctypes.POINTER(ctypes.c_int), F]
@@ -420,23 +422,27 @@ class Solver:
         return rho[:n.value].copy()
 
     def solve_logged(self, n_outer: int, m_inner: int, path=None):
-        """gid_run one outer iteration at a time, recording after each the exact
-        energy per term, the PCG rho history of its Gauss-Newton step and the
-        host wall time; returns the records and, with a path, appends them to
+        """gid_run one outer iteration at a time (PCG history recording on
+        meanwhile), recording after each the exact energy per term, the PCG rho
+        history of its Gauss-Newton step and the host wall time; returns the records and, with a path, appends them to
         it as JSON lines.  The state it reaches is the one gid_run(n_outer,
         m_inner) reaches when the base colours are refined every outer
         iteration or never (refine_base_colors 1 or 0)."""
         import json
         import time
         recs = []
-        for n in range(n_outer):
-            t0 = time.perf_counter()
-            self.run(1, m_inner)
-            total, per = self.energy()
-            rho = self.pcg_history()
-            recs.append({"outer": n + 1, "energy": total, "terms": dict(zip(ENERGY_TERMS, map(float, per))),
-                         "pcg_rho": rho.tolist(), "pcg_steps": m_inner,
-                         "wall_ms": 1000.0 * (time.perf_counter() - t0)})
+        self._chk(self.lib.gid_set_pcg_history(self.h, 1))
+        try:
+            for n in range(n_outer):
+                t0 = time.perf_counter()
+                self.run(1, m_inner)
+                total, per = self.energy()
+                rho = self.pcg_history()
+                recs.append({"outer": n + 1, "energy": total, "terms": dict(zip(ENERGY_TERMS, map(float, per))),
+                             "pcg_rho": rho.tolist(), "pcg_steps": m_inner,
+                             "wall_ms": 1000.0 * (time.perf_counter() - t0)})
+        finally:
+            self._chk(self.lib.gid_set_pcg_history(self.h, 0))
         if path is not None:
             with open(path, "a") as f:
                 for r in recs:
