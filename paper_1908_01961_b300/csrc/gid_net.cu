@@ -195,19 +195,17 @@ static void wgrad(gid_net* n, int l, const bf16* g, const bf16* in1, int up1, co
   a.W = W;
   a.taps = L.taps;
   const long P = (long)B * H * W;
-  const int WM = L.cop % 64 == 0 ? 2 : 1, BMW = 32 * WM, BNW = 128 / WM;
+  // 128 output channels x WT_BN columns per CTA, the pixels split so that the
+  // grid fills about two waves; each split is a whole number of 64-pixel chunks
   const int N = L.taps * L.ci;
-  const unsigned gx = L.cop / BMW, gy = (N + BNW - 1) / BNW;
+  const unsigned gx = (L.cop + 127) / 128, gy = (N + WT_BN - 1) / WT_BN;
   const long base = (long)gx * gy;
-  long splits = std::max(1L, std::min((592 + base - 1) / base, (P + 255) / 256));
+  long splits = std::max(1L, std::min((888 + base - 1) / base, (P + WT_BK - 1) / WT_BK));
   long chunk = (P + splits - 1) / splits;
-  chunk = (chunk + WG_BK - 1) / WG_BK * WG_BK;
+  chunk = (chunk + WT_BK - 1) / WT_BK * WT_BK;
   splits = (P + chunk - 1) / chunk;
   a.chunk = chunk;
-  if (WM == 2)
-    k_wgrad<2><<<dim3(gx, gy, (unsigned)splits), 128, 0, n->s>>>(a);
-  else
-    k_wgrad<1><<<dim3(gx, gy, (unsigned)splits), 128, 0, n->s>>>(a);
+  k_wgrad_tc<2><<<dim3(gx, gy, (unsigned)splits), 128, wgrad_tc_smem_bytes(), n->s>>>(a, n->status);
   counted(n);
   k_bias_grad<<<(unsigned)std::min(296L, std::max(1L, P / 64)), L.cop, 0, n->s>>>(g, P, L.cop, n->grad + L.b_off);
   counted(n);
@@ -466,6 +464,12 @@ extern "C" int gid_net_create(int K, const int* widths, uint64_t seed, void* str
     cudaGetLastError();
     gid_net_destroy(n);
     return nfail(nullptr, GID_ERR_CUDA, "tensor-core convolution: shared memory attribute");
+  }
+  if (cudaFuncSetAttribute(k_wgrad_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)wgrad_tc_smem_bytes()) !=
+      cudaSuccess) {
+    cudaGetLastError();
+    gid_net_destroy(n);
+    return nfail(nullptr, GID_ERR_CUDA, "tensor-core weight gradient: shared memory attribute");
   }
   n->wt = n->wb + q;
   // He-normal weights, zero biases, from the seed

@@ -13,9 +13,9 @@
 // into two tensors (the gradient of such a concatenation).  The input gradient
 // is the same kernel on the output gradient with the weights flipped in space
 // and transposed in channels.  The weight gradient is a GEMM over pixels
-// (M = output channels, N = taps x input channels) split across blocks, on
-// warp-level mma.sync m16n8k16 tiles staged by cp.async and read with ldmatrix,
-// reduced with FP32 atomics.
+// (M = output channels, N = taps x input channels) split across blocks, also
+// on the tensor cores (operands staged MN-major from the NHWC tensors), reduced
+// with FP32 atomics.
 #pragma once
 
 #include <cuda_bf16.h>
@@ -26,27 +26,7 @@ namespace gidnet {
 
 typedef __nv_bfloat16 bf16;
 
-__device__ __forceinline__ void mma16816(float* c, const uint32_t* a, const uint32_t* b) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void ldsm_x4(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-
-__device__ __forceinline__ void ldsm_x4_t(uint32_t* r, const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
 
 // 16-byte asynchronous global -> shared copy; src_bytes = 0 writes zeros.
 __device__ __forceinline__ void cp16(void* dst, const void* src, int src_bytes) {
@@ -316,113 +296,170 @@ struct WgradArgs {
   int Co;
   float* dw;  // [Co][taps][C1 + C2] fp32, accumulated
   int B, H, W, taps;
-  long chunk;  // pixels per block along grid.z (multiple of 32)
+  long chunk;  // pixels per block along grid.z (a multiple of 64)
 };
 
-constexpr int WG_BK = 32;
+// ---------------------------------------------------------------- tcgen05 weight gradient
+//
+// dW[co][n] += sum_p g[p][co] in[p + offset(tap)][ci], n = tap C_in + ci, as
+// D[M = co][N = n] = A[M][K] B[N][K]^T with K = pixels, on the 5th-generation
+// tensor cores.  Both operands come from NHWC tensors, whose channels are
+// contiguous, so both are staged MN-major: within a stage, pixel r (a K index)
+// of 64-channel block j is one 128-byte row at j * 8 KB + r * 128, its 16-byte
+// chunks swizzled by the row (chunk c at ((c ^ (r & 7)) << 4)), 8-row groups
+// 1 KB apart along K.  One CTA: 128 output channels x WT_BN columns n in tensor
+// memory, the pixels of its split in chunks of 64 (a two-stage ring of
+// cp.async copies, one thread issuing tcgen05.mma), then FP32 atomics into dW.
+// Waits are bounded; TMEM is always freed.
+constexpr int WT_BN = 128, WT_BK = 64;
 
-// dW[co][tap][ci] += sum_p g[p][co] in[p + offset(tap)][ci], as a GEMM with
-// M = co, N = n = tap * Ci + ci, K = pixels.  Block: 32 WM output channels x
-// 32 (4 / WM) columns n, 4 warps of 32 x 32; grid (Co / (32 WM), ceil(taps Ci /
-// BNW), splits) with `chunk` pixels per split.
-template <int WM>
-__global__ void __launch_bounds__(128) k_wgrad(WgradArgs a) {
-  constexpr int BMW = 32 * WM, BNW = 32 * (4 / WM), LDA = BMW + 8, LDB = BNW + 8;
-  __shared__ __align__(16) bf16 sG[2][WG_BK][LDA];
-  __shared__ __align__(16) bf16 sI[2][WG_BK][LDB];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31, g = lane >> 2, t4 = lane & 3;
-  const int wm = warp % WM, wn = warp / WM;
-  const int Ci = a.C1 + a.C2, N = a.taps * Ci;
-  const int co0 = blockIdx.x * BMW, n0 = blockIdx.y * BNW;
-  const long P = (long)a.B * a.H * a.W;
-  const long pbeg = (long)blockIdx.z * a.chunk;
-  const long pend = pbeg + a.chunk < P ? pbeg + a.chunk : P;
-  if (pbeg >= pend) return;
-  const int nsteps = (int)((pend - pbeg + WG_BK - 1) / WG_BK);
+// Shared-memory descriptor, MN-major operand, 128-byte swizzle: 64-element
+// blocks along M (or N) 8 KB apart (leading byte offset), 8-row groups along K
+// 1 KB apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t tc_desc_mn_sw128(uint32_t saddr) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(8192 >> 4) << 16) | ((uint64_t)(1024 >> 4) << 32) |
+         ((uint64_t)1 << 46) | ((uint64_t)2 << 61);
+}
 
-  auto stage = [&](int s, int buf) {
-    const long pc = pbeg + (long)s * WG_BK;
-    for (int i = tid; i < WG_BK * (BMW / 8); i += 128) {
-      const int r = i / (BMW / 8), c = (i % (BMW / 8)) * 8;
-      const long p = pc + r;
-      const bool ok = p < pend;
-      cp16(&sG[buf][r][c], ok ? a.g + p * a.Co + co0 + c : a.g, ok ? 16 : 0);
+template <int STAGES>
+__global__ void __launch_bounds__(128, 1) k_wgrad_tc(WgradArgs a, int* __restrict__ status) {
+  extern __shared__ uint8_t tc_smem_raw[];
+  __shared__ __align__(8) uint64_t bar_stage[STAGES];
+  __shared__ __align__(8) uint64_t bar_done;
+  __shared__ uint32_t tmem_slot;
+  constexpr int A_BYTES = 2 * 64 * 128, B_BYTES = (WT_BN / 64) * 64 * 128, STAGE_BYTES = A_BYTES + B_BYTES;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int Ci = a.C1 + a.C2, Ntot = a.taps * Ci;
+  const int m0 = blockIdx.x * 128, n0 = blockIdx.y * WT_BN;
+  const long P = (long)a.B * a.H * a.W, p0 = (long)blockIdx.z * a.chunk;
+  const long pend = p0 + a.chunk < P ? p0 + a.chunk : P;
+  const int nk = pend > p0 ? (int)((pend - p0 + WT_BK - 1) / WT_BK) : 0;
+  const uint32_t raw = smem_u32(tc_smem_raw);
+  uint8_t* st = tc_smem_raw + (((raw + 1023u) & ~1023u) - raw);
+  const uint32_t st_addr = smem_u32(st);
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_u32(&tmem_slot)),
+                 "r"((uint32_t)WT_BN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  if (tid == 0) {
+    for (int i = 0; i < STAGES; i++) tc_mbar_init(&bar_stage[i]);
+    tc_mbar_init(&bar_done);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot;
+
+  // stage s <- pixels p0 + 64 kc ..: A rows from g, B rows from the shifted input
+  auto load_stage = [&](int kc, int s) {
+    uint8_t* sa = st + s * STAGE_BYTES;
+    uint8_t* sb = sa + A_BYTES;
+    const long pk = p0 + (long)kc * WT_BK;
+    for (int i = tid; i < 2 * 64 * 8; i += 128) {
+      const int j = i >> 9, r = (i >> 3) & 63, c = i & 7;
+      const long p = pk + r;
+      const int co = m0 + j * 64 + c * 8;
+      const bool ok = p < pend && co < a.Co;
+      cp16(sa + j * 8192 + r * 128 + ((c ^ (r & 7)) << 4), ok ? a.g + p * a.Co + co : a.g, ok ? 16 : 0);
     }
-    for (int i = tid; i < WG_BK * (BNW / 8); i += 128) {
-      const int r = i / (BNW / 8), c = (i % (BNW / 8)) * 8;
-      const long p = pc + r;
-      const int n = n0 + c;
-      bool ok = p < pend && n < N;
+    for (int i = tid; i < (WT_BN / 64) * 64 * 8; i += 128) {
+      const int j = i >> 9, r = (i >> 3) & 63, c = i & 7;
+      const long p = pk + r;
+      const int n = n0 + j * 64 + c * 8;
       const bf16* src = a.in1;
-      if (ok) {
+      int bytes = 0;
+      if (p < pend && n < Ntot) {
         const int tap = n / Ci, ch = n - tap * Ci;
+        const Pix px = pix_of(p, a.H, a.W);
         const int dy = a.taps == 9 ? tap / 3 - 1 : 0, dx = a.taps == 9 ? tap % 3 - 1 : 0;
-        const Pix q = pix_of(p, a.H, a.W);
-        const int yy = q.y + dy, xx = q.x + dx;
-        ok = yy >= 0 && yy < a.H && xx >= 0 && xx < a.W;
-        if (ok)
-          src = ch < a.C1 ? a.in1 + tensor_off(q.b, yy, xx, a.H, a.W, a.up1, a.C1, ch)
-                          : a.in2 + tensor_off(q.b, yy, xx, a.H, a.W, 0, a.C2, ch - a.C1);
+        const int yy = px.y + dy, xx = px.x + dx;
+        if (yy >= 0 && yy < a.H && xx >= 0 && xx < a.W) {
+          src = ch < a.C1 ? a.in1 + tensor_off(px.b, yy, xx, a.H, a.W, a.up1, a.C1, ch)
+                          : a.in2 + tensor_off(px.b, yy, xx, a.H, a.W, 0, a.C2, ch - a.C1);
+          bytes = 16;
+        }
       }
-      cp16(&sI[buf][r][c], src, ok ? 16 : 0);
+      cp16(sb + j * 8192 + r * 128 + ((c ^ (r & 7)) << 4), src, bytes);
     }
-    cp_commit();
   };
 
-  float acc[2][4][4];
+  // both operands MN-major (instruction-descriptor bits 15 and 16)
+  const uint32_t idesc = tc_idesc_bf16(128, WT_BN) | (1u << 15) | (1u << 16);
+  bool waits_ok = true;
 #pragma unroll
-  for (int i = 0; i < 2; i++)
-#pragma unroll
-    for (int j = 0; j < 4; j++)
-#pragma unroll
-      for (int e = 0; e < 4; e++) acc[i][j][e] = 0.f;
-
-  stage(0, 0);
-  for (int s = 0; s < nsteps; s++) {
-    const int buf = s & 1;
-    if (s + 1 < nsteps) {
-      stage(s + 1, buf ^ 1);
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-#pragma unroll
-    for (int k0 = 0; k0 < WG_BK; k0 += 16) {
-      uint32_t A[2][4], Bf[4][2];
-#pragma unroll
-      for (int mt = 0; mt < 2; mt++)
-        ldsm_x4_t(A[mt], &sG[buf][k0 + (lane & 7) + ((lane >> 4) << 3)][wm * 32 + mt * 16 + ((lane >> 3) & 1) * 8]);
-#pragma unroll
-      for (int np = 0; np < 2; np++) {
-        uint32_t r[4];
-        ldsm_x4_t(r, &sI[buf][k0 + (lane & 7) + ((lane >> 3) & 1) * 8][wn * 32 + np * 16 + (lane >> 4) * 8]);
-        Bf[2 * np][0] = r[0];
-        Bf[2 * np][1] = r[1];
-        Bf[2 * np + 1][0] = r[2];
-        Bf[2 * np + 1][1] = r[3];
-      }
-#pragma unroll
-      for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-        for (int nt = 0; nt < 4; nt++) mma16816(acc[mt][nt], A[mt], Bf[nt]);
-    }
-    __syncthreads();
+  for (int s = 0; s < STAGES - 1; s++) {
+    if (s < nk) load_stage(s, s);
+    cp_commit();
   }
-
+  for (int kc = 0; kc < nk; kc++) {
+    const int s = kc % STAGES;
+    cp_wait<STAGES - 2>();
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+      const uint32_t sa = st_addr + s * STAGE_BYTES, sb = sa + A_BYTES;
 #pragma unroll
-  for (int mt = 0; mt < 2; mt++)
-#pragma unroll
-    for (int h = 0; h < 2; h++) {
-      const int co = co0 + wm * 32 + mt * 16 + g + 8 * h;
-#pragma unroll
-      for (int nt = 0; nt < 4; nt++) {
-        const int n = n0 + wn * 32 + nt * 8 + 2 * t4;
-        if (n < N) atomicAdd(a.dw + (long)co * N + n, acc[mt][nt][2 * h]);
-        if (n + 1 < N) atomicAdd(a.dw + (long)co * N + n + 1, acc[mt][nt][2 * h + 1]);
+      for (int kk = 0; kk < WT_BK / 16; kk++) {  // 16 pixels = two 8-row groups per instruction
+        const uint64_t ad = tc_desc_mn_sw128(sa + kk * 2048), bd = tc_desc_mn_sw128(sb + kk * 2048);
+        const uint32_t acc = (kc | kk) != 0 ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
       }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&bar_stage[s]))
+                   : "memory");
     }
+    const int nxt = kc + STAGES - 1;
+    if (nxt < nk) {
+      const int ns = nxt % STAGES;
+      if (kc >= 1) waits_ok &= tc_mbar_wait(&bar_stage[ns], (unsigned)(((kc - 1) / STAGES) & 1));
+      load_stage(nxt, ns);
+    }
+    cp_commit();
+  }
+  if (nk > 0) {
+    if (tid == 0)
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                       smem_u32(&bar_done))
+                   : "memory");
+    waits_ok &= tc_mbar_wait(&bar_done, 0u);
+    tc_fence_after();
+    // epilogue: TMEM lane 32 w + lane is output channel m0 + 32 w + lane
+    const int co = m0 + warp * 32 + (tid & 31);
+    for (int j = 0; j < WT_BN; j += 16) {
+      uint32_t r[16];
+      const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)j;
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+      if (co >= a.Co) continue;
+      float* row = a.dw + (long)co * Ntot + n0 + j;
+#pragma unroll
+      for (int e = 0; e < 16; e += 4)
+        if (n0 + j + e < Ntot)
+          atomicAdd(reinterpret_cast<float4*>(row + e), make_float4(__uint_as_float(r[e]), __uint_as_float(r[e + 1]),
+                                                                   __uint_as_float(r[e + 2]), __uint_as_float(r[e + 3])));
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"((uint32_t)WT_BN) : "memory");
+  if (!waits_ok) atomicOr(status, 1);
 }
+
+constexpr size_t wgrad_tc_smem_bytes() { return 2 * (2 * 64 * 128 + (WT_BN / 64) * 64 * 128) + 1024; }
 
 // db[c] += sum_p g[p][c]; blockDim.x == C.
 __global__ void k_bias_grad(const bf16* __restrict__ g, long P, int C, float* __restrict__ db) {
