@@ -1115,10 +1115,11 @@ __device__ __forceinline__ float update_range(const Params& P, const float* __re
 // block partials of rho' = <r, z> = sum z^2 / M^-1.  last 1: X += delta + alpha p
 // (the Gauss-Newton update); last 2: write delta only.  Works on whole pitched
 // planes as float4 (the padding columns of every PCG vector are zero and stay
-// zero).  A grid of a few blocks per SM strides over all V x plane / 4 float4
-// items.
+// zero).  A grid of two blocks per SM strides over all V x plane / 4 float4
+// items; a 64-register cap for four blocks per SM spilled and measured 10 %
+// slower.
 template <int K>
-__global__ void __launch_bounds__(256, 4) k_update(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
+__global__ void __launch_bounds__(256, 2) k_update(Params P, int it, int nb_prev, const float* __restrict__ p, int last) {
   grid_dep_wait();  // the operator step's p, q and partials
   grid_dep_release();
   // alpha = rho_it / <p, q>_it from the operator step's partials
