@@ -237,15 +237,34 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 
 /* ---- operator tile shape ---- */
 
-/* How the PCG loop runs.  rows = 2, 4 (default), 8 or 17: one operator kernel
- * and one vector kernel per PCG step, operator tiles of 128 x rows pixels
- * (17 runs one 544-thread block per SM).  rows = 0: all PCG steps of a
- * Gauss-Newton step in one cooperative launch (one block per SM, operator and
- * vector phases separated by grid barriers whose waits are bounded; a barrier
- * that gives up is reported as GID_ERR_TIMEOUT by the next synchronising
- * call); GID_ERR_INVALID_ARG if the device cannot co-schedule it.  Results
- * agree to FP32 rounding order; only speed differs. */
+/* How the PCG loop of each Gauss-Newton step (Sec. 6.1) runs.  rows = 2, 4
+ * (default), 8 or 17: one operator kernel and one vector kernel per PCG step,
+ * operator tiles of 128 x rows pixels (17 runs one 544-thread block per SM).
+ * rows = 0: all PCG steps of a Gauss-Newton step in one cooperative launch
+ * (one block per SM streaming every vector, operator and vector phases
+ * separated by grid barriers whose waits are bounded; a barrier that gives up
+ * is reported as GID_ERR_TIMEOUT by the next synchronising call).
+ * rows = GID_PCG_RESIDENT: one cooperative launch as well, in which each block
+ * owns one tile of the frame for the whole Gauss-Newton step and keeps that
+ * tile's z (with the stencil's halo) and p in shared memory; only q, delta,
+ * M^-1 and the operator coefficients stream through L2, and neighbouring
+ * tiles exchange the border rows and columns of z through a global buffer
+ * after every vector phase.  It needs the whole frame's tiles co-resident (one
+ * block per SM), so it exists only for frames up to a few hundred thousand
+ * pixels (640 x 480 at K = 6 is 148 tiles of 160 x 13 on 148 SMs); the first
+ * selection allocates its exchange buffers (V planes + 12 KB) and synchronises.
+ * Jacobi preconditioner only (GID_PRECOND_BLOCK keeps the two-kernel loop).
+ * GID_ERR_INVALID_ARG if the device cannot co-schedule the chosen loop or the
+ * frame does not fit.  Results agree to FP32 rounding order; only speed
+ * differs. */
+#define GID_PCG_RESIDENT (-1)
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
+
+/* The context's PCG loop (*rows as passed to gid_set_apply_tile) and the tile
+ * geometry the resident loop has, or would have, on this frame: tile_w x
+ * tile_h pixels, `blocks` tiles (0, 0, 0 if it does not fit).  Any pointer may
+ * be NULL. */
+int gid_get_pcg_layout(gid_ctx* ctx, int* rows, int* tile_w, int* tile_h, int* blocks);
 
 /* ---- PCG history ---- */
 
@@ -270,8 +289,9 @@ int gid_pcg_history(gid_ctx* ctx, double* rho_host, int max_n, int* n_out);
 
 /* Host-side fault injection for failure-detection tests (the paper has no
  * counterpart).  phantom_blocks > 0 adds that many participants that never
- * arrive to every grid barrier of the persistent PCG kernel
- * (gid_set_apply_tile(0)), so every block's bounded wait runs out; spin_limit
+ * arrive to every grid barrier of the persistent and resident PCG kernels
+ * (gid_set_apply_tile(0) or GID_PCG_RESIDENT), so every block's bounded wait
+ * runs out; spin_limit
  * > 0 replaces the barrier's poll limit (default 2^22 polls of about 64 ns),
  * so that the wait gives up after spin_limit polls.  A barrier that gives up
  * records a status bit and its kernel returns without updating the state; the
@@ -304,11 +324,13 @@ int gid_set_preconditioner(gid_ctx* ctx, int kind);
 /* The context's preconditioner (GID_PRECOND_*), -1 for a NULL ctx. */
 int gid_get_preconditioner(const gid_ctx* ctx);
 
-/* Time reps PCG steps with each of the five ways above on the current frame
+/* Time reps PCG steps with each of the six ways above on the current frame
  * and state (CUDA events on the context stream) and keep the fastest.  Writes
- * the chosen rows (0 = persistent) to *rows_out and the five timings (us per
- * PCG step; shapes 2, 4, 8, 17, persistent, -1 if unavailable) to us_out[5];
- * either may be NULL.  Needs gid_set_frame and a state; leaves the state X
+ * the chosen rows (0 = persistent, GID_PCG_RESIDENT) to *rows_out and the six
+ * timings (us per PCG step; shapes 2, 4, 8, 17, persistent, resident, -1 if
+ * unavailable) to us_out[6]; either may be NULL.  The single-launch loops are
+ * timed as the difference of two Gauss-Newton steps (reps + 2 and 2 PCG
+ * steps), so that the linearisation does not count.  Needs gid_set_frame and a state; leaves the state X
  * unchanged (the PCG vectors are scratch until the next gid_run).  Call it
  * between runs.  Synchronises. */
 int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);

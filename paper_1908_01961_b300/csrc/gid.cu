@@ -59,6 +59,14 @@ struct gid_ctx {
   int upd_cap = 148 * 4;   // vector-step blocks resident at once (SMs x blocks per SM)
   int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
+  bool resident = false;   // resident PCG kernel selected (gid_set_apply_tile(-1) / gid_autotune)
+  ResTile res{};           // its tile geometry; res_blocks = 0 if the frame does not fit on chip
+  CUtensorMap res_map;     // its coefficient stream: box [1 plane][TH + 1 rows][4 TX + 8 columns]
+  int res_blocks = 0, res_threads = 0;
+  size_t res_smem = 0;
+  bool res_planned = false;
+  float* zx = nullptr;     // its border exchange planes (2 x V planes, allocated on first use)
+  double* xval = nullptr;  // its all-reduce slots [RES_ROWS][RES_NV][RES_MAXB] and arrival counters
   int last_m_inner = 0;    // PCG steps of the latest Gauss-Newton step (gid_pcg_history)
   bool record_rho = false;  // copy each PCG step's rho into the history (gid_set_pcg_history)
   bool hist_valid = false;  // the latest Gauss-Newton step recorded its history
@@ -67,7 +75,7 @@ struct gid_ctx {
   int blk_blocks = 0;       // grid of the block-Jacobi vector step
   // CUDA graphs of gid_run's launch sequence, replayed on a context-owned stream
   struct Graph {
-    int n, m, refine, temporal, th;
+    int n, m, refine, temporal, th, kernel;
     cudaGraphExec_t exec;
     long long kernels;
   };
@@ -186,7 +194,17 @@ static Params params(const gid_ctx* c) {
   P.partial = c->partial;
   P.pcg_part = c->pcg_part;
   P.nbmax = c->nbmax;
+  P.zx = c->zx;
+  P.xval = c->xval;
   return P;
+}
+
+// How the PCG loop of a Gauss-Newton step runs: 0 one operator and one vector
+// kernel per step, 1 the persistent cooperative kernel, 2 the resident one.
+static int pcg_kernel(const gid_ctx* c) {
+  if (c->resident && c->res_blocks > 0) return 2;
+  if (c->persistent && c->pcg_blocks > 0) return 1;
+  return 0;
 }
 
 static dim3 pix_grid(const gid_ctx* c) { return dim3((c->W + BX - 1) / BX, (c->H + BY - 1) / BY); }
@@ -330,6 +348,73 @@ struct Launch {
         cudaSuccess)
       return 0;
     return coop ? sms * per_sm : 0;
+  }
+  // The resident PCG loop: one cooperative launch of res_blocks blocks.
+  static cudaError_t resident(const gid_ctx* c, int m_inner, int last_mode) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(c->res_blocks);
+    cfg.blockDim = dim3(c->res_threads);
+    cfg.dynamicSmemBytes = c->res_smem;
+    cfg.stream = c->stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pcg_resident<K>, params(c), c->res, m_inner, last_mode, c->q, c->res_map);
+  }
+  // Tile geometry of the resident PCG kernel for this frame on this device:
+  // among tiles of 4 TX x TH pixels (TX x TH <= RES_MAXT threads, shared
+  // memory within the per-block limit) whose count fits the co-resident
+  // blocks, the smallest tile (every phase waits for the slowest block) but
+  // none below 512 pixels while fewer blocks can do (small frames: fewer
+  // participants in every grid barrier), then the fewest blocks, then the
+  // smallest staged halo.  res_blocks stays 0 if none fits.
+  static void res_plan(gid_ctx* c) {
+    c->res_planned = true;
+    c->res_blocks = 0;
+    int dev = 0, sms = 0, coop = 0, optin = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa;
+    if (!coop || sms < 1 || cudaFuncGetAttributes(&fa, k_pcg_resident<K>) != cudaSuccess) return;
+    const long limit = (long)optin - (long)fa.sharedSizeBytes;
+    long best_area = -1, best_halo = 0, best_nb = 0;
+    ResTile best{};
+    for (int TX = 2; res_threads(TX, 1) <= RES_MAXT; TX++)
+      for (int TH = 1; res_threads(TX, TH) <= RES_MAXT; TH++) {
+        const long smem = res_smem_bytes(K, TX, TH);
+        if (smem > limit) break;
+        const long ntx = (c->W + 4 * TX - 1) / (4 * TX), nb = ntx * ((c->H + TH - 1) / TH);
+        if (nb > sms) continue;
+        const long area = std::max(4L * TX * TH, 512L), halo = (4L * TX + 8) * (TH + 6) - 4L * TX * TH;
+        if (best_area < 0 || area < best_area || (area == best_area && nb < best_nb) ||
+            (area == best_area && nb == best_nb && halo < best_halo)) {
+          best_area = area;
+          best_halo = halo;
+          best_nb = nb;
+          best = ResTile{TX, TH, (int)ntx, 4 * TX + 8};
+        }
+      }
+    if (best_area < 0) return;
+    const size_t smem = (size_t)res_smem_bytes(K, best.TX, best.TH);
+    const int threads = res_threads(best.TX, best.TH);
+    int per_sm = 0;
+    if (cudaFuncSetAttribute(k_pcg_resident<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_resident<K>, threads, smem) != cudaSuccess ||
+        per_sm < 1) {
+      cudaGetLastError();
+      return;
+    }
+    const int nb = best.ntx * ((c->H + best.TH - 1) / best.TH);
+    if (nb > sms * per_sm || nb > RES_MAXB) return;
+    c->res = best;
+    c->res_threads = threads;
+    c->res_smem = smem;
+    c->res_blocks = nb;
   }
   // Resident blocks of the base-colour step on this device (SMs x blocks per SM).
   static int dense_capacity(const gid_ctx*) {
@@ -611,6 +696,8 @@ extern "C" void gid_destroy(gid_ctx* c) {
   }
   cudaFree(c->pool);
   cudaFree(c->blk);
+  cudaFree(c->zx);
+  cudaFree(c->xval);
   cudaFree(c->st_rgb);
   cudaFree(c->st_lab);
   cudaFree(c->st_R);
@@ -758,7 +845,7 @@ static void record_rho(gid_ctx* c, int m) {
 
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   c->last_m_inner = m_inner;
-  c->hist_valid = c->record_rho || (c->persistent && c->pcg_blocks > 0 && c->precond == GID_PRECOND_JACOBI);
+  c->hist_valid = c->record_rho || (pcg_kernel(c) != 0 && c->precond == GID_PRECOND_JACOBI);
   if (c->precond == GID_PRECOND_BLOCK) {
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 3, (float*)nullptr, (float*)nullptr); });
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, block_factor, c); });
@@ -774,7 +861,26 @@ static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   }
   launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
   if (int rc = check_launch(c, "k_linearize")) return rc;
-  if (c->persistent && c->pcg_blocks > 0) {
+  if (pcg_kernel(c) == 2) {
+    cudaError_t e = cudaSuccess;
+    launch(c, GID_KIND_PCG, [&] {
+      switch (c->K) {
+        case 1: e = Launch<1>::resident(c, m_inner, last_mode); break;
+        case 2: e = Launch<2>::resident(c, m_inner, last_mode); break;
+        case 3: e = Launch<3>::resident(c, m_inner, last_mode); break;
+        case 4: e = Launch<4>::resident(c, m_inner, last_mode); break;
+        case 5: e = Launch<5>::resident(c, m_inner, last_mode); break;
+        case 6: e = Launch<6>::resident(c, m_inner, last_mode); break;
+        case 7: e = Launch<7>::resident(c, m_inner, last_mode); break;
+        case 8: e = Launch<8>::resident(c, m_inner, last_mode); break;
+        case 9: e = Launch<9>::resident(c, m_inner, last_mode); break;
+        default: e = Launch<10>::resident(c, m_inner, last_mode); break;
+      }
+    });
+    if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, "k_pcg_resident (cooperative launch)", cudaGetErrorString(e));
+    return check_launch(c, "k_pcg_resident");
+  }
+  if (pcg_kernel(c) == 1) {
     cudaError_t e = cudaSuccess;
     launch(c, GID_KIND_PCG, [&] {
       switch (c->K) {
@@ -827,7 +933,8 @@ static int run_graph(gid_ctx* c, int n_outer, int m_inner, bool refine) {
   const int temporal = c->temporal_active ? 1 : 0;
   gid_ctx::Graph* g = nullptr;
   for (auto& e : c->graphs)
-    if (e.n == n_outer && e.m == m_inner && e.refine == (int)refine && e.temporal == temporal && e.th == c->apply_th)
+    if (e.n == n_outer && e.m == m_inner && e.refine == (int)refine && e.temporal == temporal && e.th == c->apply_th &&
+        e.kernel == pcg_kernel(c))
       g = &e;
   if (!g) {
     cudaStream_t user = c->stream;
@@ -848,7 +955,7 @@ static int run_graph(gid_ctx* c, int n_outer, int m_inner, bool refine) {
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
     if (e != cudaSuccess) return fail(c, GID_ERR_CUDA, "cudaGraphInstantiate", cudaGetErrorString(e));
-    c->graphs.push_back({n_outer, m_inner, (int)refine, temporal, c->apply_th, exec, c->launches - l0});
+    c->graphs.push_back({n_outer, m_inner, (int)refine, temporal, c->apply_th, pcg_kernel(c), exec, c->launches - l0});
     c->launches = l0;
     g = &c->graphs.back();
   }
@@ -1152,17 +1259,78 @@ extern "C" int gid_profile_read(gid_ctx* c, double* ms, long long* count) {
 
 // ---------------------------------------------------------------- operator tile shape
 
+// Plans the resident PCG kernel for the context's frame (once) and allocates
+// its exchange buffers on first use.  GID_ERR_INVALID_ARG if it does not fit.
+static int res_prepare(gid_ctx* c) {
+  if (!c->res_planned) GID_DISPATCH(c, res_plan, c);
+  if (c->res_blocks <= 0)
+    return fail(c, GID_ERR_INVALID_ARG,
+                "the resident PCG kernel does not fit this frame on this device (its tiles of the PCG state "
+                "exceed one block per SM)");
+  if (!c->zx) {
+    // the coefficient planes as a 3-D tensor (columns, rows, planes); one box is
+    // one plane of a tile with the row above and 4 columns to the left
+    auto fn = encode_fn();
+    const int nc = coef_planes(c->K, c->w.n_spatial_pairs);
+    const cuuint64_t dims[3] = {(cuuint64_t)c->pitch, (cuuint64_t)c->H, (cuuint64_t)nc};
+    const cuuint64_t strides[2] = {(cuuint64_t)c->pitch * sizeof(float), (cuuint64_t)c->plane * sizeof(float)};
+    const cuuint32_t box[3] = {(cuuint32_t)(4 * c->res.TX + 8), (cuuint32_t)(c->res.TH + 1), 1u};
+    const cuuint32_t es[3] = {1u, 1u, 1u};
+    if (!fn || fn(&c->res_map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->coef, dims, strides, box, es,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return fail(c, GID_ERR_CUDA, "cuTensorMapEncodeTiled failed for the resident coefficient stream");
+  }
+  if (!c->zx) {
+    const size_t zb = 2 * (size_t)c->V * c->plane * sizeof(float);
+    const size_t xb = (size_t)RES_ROWS * RES_NV * RES_MAXB * sizeof(double) + RES_ROWS * 128;
+    if (cudaMalloc(&c->zx, zb) != cudaSuccess || cudaMalloc(&c->xval, xb) != cudaSuccess) {
+      cudaGetLastError();
+      cudaFree(c->zx);
+      cudaFree(c->xval);
+      c->zx = nullptr;
+      c->xval = nullptr;
+      return fail(c, GID_ERR_OOM, "resident PCG exchange buffers");
+    }
+    // the exchange planes' padding columns and unowned chunks read as zero; the
+    // all-reduce counters are cleared by every linearisation
+    GID_TRY_CUDA(c, cudaMemsetAsync(c->zx, 0, zb, c->stream));
+    GID_TRY_CUDA(c, cudaMemsetAsync(c->xval, 0, xb, c->stream));
+    GID_TRY_CUDA(c, cudaStreamSynchronize(c->stream));
+  }
+  return GID_OK;
+}
+
 extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if (rows == GID_PCG_RESIDENT) {
+    if (int rc = res_prepare(c)) return rc;
+    c->resident = true;
+    c->persistent = false;
+    return GID_OK;
+  }
   if (rows == 0) {
     if (c->pcg_blocks <= 0) return fail(c, GID_ERR_INVALID_ARG, "the persistent PCG kernel cannot run on this device");
     c->persistent = true;
+    c->resident = false;
     return GID_OK;
   }
   if (rows != 2 && rows != 4 && rows != 8 && rows != 17)
-    return fail(c, GID_ERR_INVALID_ARG, "tile rows must be 0 (persistent), 2, 4, 8 or 17");
+    return fail(c, GID_ERR_INVALID_ARG, "tile rows must be -1 (resident), 0 (persistent), 2, 4, 8 or 17");
   c->apply_th = rows;
   c->persistent = false;
+  c->resident = false;
+  return GID_OK;
+}
+
+extern "C" int gid_get_pcg_layout(gid_ctx* c, int* rows, int* tile_w, int* tile_h, int* blocks) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  const int k = pcg_kernel(c);
+  if (rows) *rows = k == 2 ? GID_PCG_RESIDENT : (k == 1 ? 0 : c->apply_th);
+  if (!c->res_planned) GID_DISPATCH(c, res_plan, c);
+  if (tile_w) *tile_w = c->res_blocks > 0 ? 4 * c->res.TX : 0;
+  if (tile_h) *tile_h = c->res_blocks > 0 ? c->res.TH : 0;
+  if (blocks) *blocks = c->res_blocks;
   return GID_OK;
 }
 
@@ -1290,28 +1458,54 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
     }
   }
   c->apply_th = best_th;
-  // the persistent PCG kernel (tile rows 17, one block per SM): reps + 2 steps in one launch
-  bool pers = false;
+  // the single-launch loops (persistent, resident): the time of a Gauss-Newton
+  // step of reps + 2 PCG steps less that of one of 2, per PCG step (the
+  // linearisation and the launch cancel)
+  auto time_loop = [&](float* us) -> int {
+    float ms[2] = {0.f, 0.f};
+    for (int i = 0; i < 2; i++) {
+      cudaEventRecord(e0, c->stream);
+      if (int rc = enqueue_gn_step(c, i == 0 ? 2 : reps + 2, 2)) return rc;
+      cudaEventRecord(e1, c->stream);
+      GID_TRY_CUDA(c, cudaEventSynchronize(e1));
+      GID_TRY_CUDA(c, cudaEventElapsedTime(&ms[i], e0, e1));
+    }
+    *us = 1000.f * (ms[1] - ms[0]) / reps;
+    return sync_status(c);
+  };
+  int choice = best_th;  // rows, 0 persistent, GID_PCG_RESIDENT resident
+  c->resident = false;
   if (c->pcg_blocks > 0) {
     c->persistent = true;
-    if (int rc = enqueue_gn_step(c, 2, 2)) return rc;
-    cudaEventRecord(e0, c->stream);
-    if (int rc = enqueue_gn_step(c, reps + 2, 2)) return rc;
-    cudaEventRecord(e1, c->stream);
-    GID_TRY_CUDA(c, cudaEventSynchronize(e1));
-    float ms = 0.f;
-    GID_TRY_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-    const float us = 1000.f * ms / (reps + 2);
+    float us = 0.f;
+    if (int rc = time_loop(&us)) return rc;
     if (us_out) us_out[4] = us;
-    pers = us < best;
-    c->persistent = pers;
-    if (int rc = sync_status(c)) return rc;
+    if (us < best) {
+      best = us;
+      choice = 0;
+    }
+    c->persistent = false;
   } else if (us_out) {
     us_out[4] = -1.f;
   }
+  if (c->precond == GID_PRECOND_JACOBI && res_prepare(c) == GID_OK) {
+    c->resident = true;
+    float us = 0.f;
+    if (int rc = time_loop(&us)) return rc;
+    if (us_out) us_out[5] = us;
+    if (us < best) {
+      best = us;
+      choice = GID_PCG_RESIDENT;
+    }
+    c->resident = false;
+  } else if (us_out) {
+    us_out[5] = -1.f;
+  }
+  c->persistent = choice == 0;
+  c->resident = choice == GID_PCG_RESIDENT;
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
-  if (rows_out) *rows_out = pers ? 0 : best_th;
+  if (rows_out) *rows_out = choice;
   return GID_OK;
 }
 

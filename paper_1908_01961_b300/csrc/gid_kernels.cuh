@@ -91,16 +91,37 @@ struct Params {
   double* partial;
   double* pcg_part;  // [2 kinds: operator <p,q>, vector <r,z>][2 parities][nbmax] block partials
   int nbmax;
+  // resident PCG kernel: border exchange planes (2 x V planes, pitched) and the
+  // grid all-reduce slots [RES_ROWS][RES_NV][RES_MAXB] followed by the arrival
+  // counters (RES_ROWS, each on its own 128-byte line)
+  float* zx;
+  double* xval;
 };
+// most blocks of one resident PCG launch (one per SM)
+constexpr int RES_MAXB = 1024;
+constexpr int RES_ROWS = 4, RES_NV = 3;
 
 // ---------------------------------------------------------------- reductions
 
 __device__ __forceinline__ int tid_flat() { return threadIdx.y * blockDim.x + threadIdx.x; }
 
-// Sum of v over the block; the result is valid in thread 0.  All threads call.
-// FP64 throughout (used for the cross-block totals).
-__device__ __forceinline__ double block_sum(double v) {
-  __shared__ double sh[32];
+// FP64 arithmetic runs at a small fraction of the FP32 rate on this part (a
+// warp-wide FP64 add holds the FP64 pipe for many cycles), so every block
+// reduction below does its FP64 additions in warp 0 only: a 5-level shuffle
+// tree over at most 32 values, in a fixed order.
+
+// FP64 shuffle tree over warp 0 (the caller is warp 0); the sum in lane 0.
+__device__ __forceinline__ double warp_tree(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum of per-thread FP32 partials: an FP32 shuffle tree inside each warp
+// (32 terms, pairwise), then the warp sums added in FP64 by warp 0's tree.
+// Valid in thread 0.  All threads call.
+__device__ __forceinline__ double block_sum_f(float v) {
+  __shared__ float sh[32];
   const int t = tid_flat(), lane = t & 31, wid = t >> 5;
   const int nw = (blockDim.x * blockDim.y + 31) >> 5;
 #pragma unroll
@@ -108,27 +129,7 @@ __device__ __forceinline__ double block_sum(double v) {
   if (lane == 0) sh[wid] = v;
   __syncthreads();
   double s = 0.0;
-  if (t == 0)
-    for (int i = 0; i < nw; i++) s += sh[i];
-  __syncthreads();
-  return s;
-}
-
-// Block sum of per-thread FP32 partials: an FP32 shuffle tree inside each warp
-// (32 terms, pairwise), then the warp sums added in FP64 in warp order.  FP64
-// arithmetic runs at a small fraction of the FP32 rate on this part, so FP64 is
-// kept to the few cross-warp and cross-block additions.  Valid in thread 0.
-__device__ __forceinline__ double block_sum_f(float v) {
-  __shared__ double sh[32];
-  const int t = tid_flat(), lane = t & 31, wid = t >> 5;
-  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane == 0) sh[wid] = (double)v;
-  __syncthreads();
-  double s = 0.0;
-  if (t == 0)
-    for (int i = 0; i < nw; i++) s += sh[i];
+  if (wid == 0) s = warp_tree(lane < nw ? (double)sh[lane] : 0.0);
   __syncthreads();
   return s;
 }
@@ -150,54 +151,51 @@ __device__ __forceinline__ bool last_block(unsigned int* cnt, unsigned int n = 0
   return is_last;
 }
 
-// Sum of n partials (stride `stride`, starting at `base`) in a fixed order.
-// Loads are issued four at a time so the last block is not latency bound.
-__device__ __forceinline__ double grid_total(const double* partial, int n, int stride, int base) {
-  const int nt = blockDim.x * blockDim.y;
-  double s = 0.0;
-  int i = tid_flat();
-  for (; i + 3 * nt < n; i += 4 * nt) {
-    const double a0 = __ldcg(partial + (long)i * stride + base);
-    const double a1 = __ldcg(partial + (long)(i + nt) * stride + base);
-    const double a2 = __ldcg(partial + (long)(i + 2 * nt) * stride + base);
-    const double a3 = __ldcg(partial + (long)(i + 3 * nt) * stride + base);
-    s += a0;
-    s += a1;
-    s += a2;
-    s += a3;
-  }
-  for (; i < n; i += nt) s += __ldcg(partial + (long)i * stride + base);
-  return block_sum(s);
-}
-
 // The PCG scalars are formed by the kernel that consumes them: every block sums
 // the previous kernel's block partials in the same fixed order (so all blocks
 // agree bit for bit), and no kernel of the PCG loop has a serial last-block
-// tail.  part_share is a thread's share (loads issued early), block_total the
-// block-wide sum returned to every thread.
+// tail.  part_share: lane l of warp 0 adds part[l], part[l + 32], ... (its
+// loads may be issued early; 0 in the other warps); block_total: warp 0's tree
+// of those shares, returned to every thread of the block.
 __device__ __forceinline__ double part_share(const double* part, int n) {
   double s = 0.0;
-  const int nt = blockDim.x * blockDim.y;
-  for (int i = tid_flat(); i < n; i += nt) s += __ldcg(part + i);
+  const int t = tid_flat();
+  if (t < 32)
+    for (int i = t; i < n; i += 32) s += __ldcg(part + i);
   return s;
 }
 
 __device__ __forceinline__ double block_total(double v) {
-  __shared__ double sh[32];
   __shared__ double tot;
-  const int t = tid_flat(), lane = t & 31, wid = t >> 5;
-  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  if (lane == 0) sh[wid] = v;
-  __syncthreads();
-  if (t == 0) {
-    double s = 0.0;
-    for (int i = 0; i < nw; i++) s += sh[i];
-    tot = s;
+  const int t = tid_flat();
+  if (t < 32) {
+    v = warp_tree(v);
+    if (t == 0) tot = v;
   }
   __syncthreads();
-  return tot;
+  const double r = tot;
+  __syncthreads();
+  return r;
+}
+
+// Sum of n partials (stride `stride`, starting at `base`) in a fixed order,
+// valid in thread 0: lane l of warp 0 adds partials l, l + 32, ... into four
+// interleaved accumulators (loads in flight together), combined in order.
+__device__ __forceinline__ double grid_total(const double* partial, int n, int stride, int base) {
+  double s = 0.0;
+  const int t = tid_flat();
+  if (t < 32) {
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    int i = t;
+    for (; i + 96 < n; i += 128) {
+#pragma unroll
+      for (int u = 0; u < 4; u++) a[u] += __ldcg(partial + (long)(i + 32 * u) * stride + base);
+    }
+    for (; i < n; i += 32) a[0] += __ldcg(partial + (long)i * stride + base);
+    s = warp_tree((a[0] + a[1]) + (a[2] + a[3]));
+  }
+  __syncthreads();
+  return s;
 }
 
 __device__ __forceinline__ double* pcg_partials(const Params& P, int kind, int it) {
@@ -542,10 +540,16 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
     mbar_expect_tx(&bar, (unsigned)sizeof(sX));
     tma_load_3d(&sX[0][0][0], &mapX, x0 - 4, y0 - 3, 0, &bar);
   }
-  {
-    bool done = false;
-    for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
-    if (!done && tid_flat() == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+  bool staged = false;
+  for (long i = 0; i < TMA_SPINS && !staged; i++) staged = mbar_try_wait(&bar, 0);
+  if (!__syncthreads_and(staged)) {
+    // the copy did not complete in time: record it and give the copy still in
+    // flight into this block's shared memory a second bounded wait; the block
+    // then writes no state (its partial of rho is zero, so the grid reduction
+    // below still counts every block)
+    if (tid_flat() == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+    for (long i = 0; i < TMA_SPINS && !staged; i++) staged = mbar_try_wait(&bar, 0);
+    staged = false;
   }
   // X reads go to the tile: the same indexing helpers with the tile's strides
   // and a base that maps absolute (y, x) into it
@@ -556,13 +560,16 @@ __global__ void __launch_bounds__(NT, K <= 6 ? 4 : 1) k_linearize(Params P, int 
   const Weights& w = P.w;
   const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
   float rz = 0.f;
+  // the resident PCG launch that follows starts with cleared arrival counters
+  if (P.xval && blockIdx.x == 0 && blockIdx.y == 0 && tid_flat() < 32 * RES_ROWS)
+    reinterpret_cast<unsigned int*>(P.xval + (long)RES_ROWS * RES_NV * RES_MAXB)[tid_flat()] = 0u;
   if ((mode == 0 || mode == 3) && x >= P.W && x < P.pitch && y < P.H) {
     // the PCG vectors' padding columns restart at zero every Gauss-Newton step
     const long o = off2(P, y, x);
 #pragma unroll
     for (int v = 0; v < V; v++) P.z[v * P.plane + o] = P.d[v * P.plane + o] = P.Minv[v * P.plane + o] = 0.f;
   }
-  if (x < P.W && y < P.H) {
+  if (staged && x < P.W && y < P.H) {
     const Pix px = make_pix(P, x, y);
     const long o = off2(P, y, x), oq = off2(Q, y, x);
     PixState<K> s;
@@ -741,6 +748,10 @@ __device__ __forceinline__ float dot4(F4 x, F4 y) {
   return t.x + t.y;
 }
 __device__ __forceinline__ F4 ldg4(const float* p) { return f4(*reinterpret_cast<const float4*>(p)); }
+// load through the read-only path: for data no thread of the kernel writes (the
+// operator coefficients, M^-1), which frees the compiler to issue it ahead of
+// the kernel's stores
+__device__ __forceinline__ F4 ldc4(const float* p) { return f4(__ldg(reinterpret_cast<const float4*>(p))); }
 __device__ __forceinline__ F4 lds4(const float* p) { return f4(*reinterpret_cast<const float4*>(p)); }
 
 // Tile of the operator kernel: 128 x 8 pixels per 32 x 8 block, four
@@ -781,6 +792,125 @@ template <>
 struct ApplyShape<17> {
   static constexpr int MINB = 1, MAXREG = 96;
 };
+
+// q = A s at one thread's four pixels (x .. x + 3 of row y, x < W, y < H), A =
+// J^T J at the Gauss-Newton step's linearisation point given by the
+// coefficient planes (CoefLayout), s read from a staged tile: reflectance
+// channel c at sr[c * SRC + dy * SRR + dx] and layer k at st[k * STC + dy * STR +
+// dx] for the offset (dy, dx) from the first pixel (sr and st point at that
+// pixel; the tile holds s with a halo of 3 rows and 4 columns for the
+// reflectance channels, 1 row and 4 columns for the layers, zero outside the
+// frame).  finish(v, s_v, (A s)_v) is called once per plane v (reflectance
+// channels first) with the four pixels' values; lanes past the frame's right
+// edge of A s are zero.  ROLL: the layer loop is not unrolled (register budget).
+// SHFL: the left neighbour's right-edge weights come from lane - 1 of the warp
+// where left_lane says that lane holds the chunk to the left (every lane of the
+// warp must then make the call); elsewhere they are loaded.
+template <int K, bool ROLL, bool SHFL = false, class FIN>
+__device__ __forceinline__ void op_apply4(const Params& P, const ColorTable<K>& ct, int x, int y,
+                                          const float* sr, int SRC, int SRR, const float* st, int STC, int STR,
+                                          FIN finish, bool left_lane = false) {
+  using CL = CoefLayout<K>;
+  const long o = off2(P, y, x);
+  const float* __restrict__ cf = P.coef + o;
+  const long PL = P.plane;
+  const bool hL = x > 0, hU = y > 0;
+  const F4 valid = f4v(1.f, x + 1 < P.W ? 1.f : 0.f, x + 2 < P.W ? 1.f : 0.f, x + 3 < P.W ? 1.f : 0.f);
+  // data block: P_c = sum_k b_kc p_Tk
+  F4 u[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) u[c] = f4s(0.f);
+#pragma unroll
+  for (int k = 0; k <= K; k++) {
+    const F4 pk = lds4(st + k * STC);
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fma4(f4s(ct.b[k][c]), pk, u[c]);
+  }
+  // reflectance channels, one at a time: data, clustering/temporal diagonal,
+  // r-sparsity, consistency pairs (x, x + o_j) and (x - o_j, x); the shared
+  // per-pixel weights are re-read through L1 rather than held in registers
+  float eLm;
+  if constexpr (SHFL) {
+    const float sh = __shfl_up_sync(0xffffffffu, cf[CL::WR * PL + 3], 1);
+    eLm = left_lane ? sh : (hL ? cf[CL::WR * PL - 1] : 0.f);
+  } else {
+    eLm = hL ? cf[CL::WR * PL - 1] : 0.f;
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    const F4 Sc = ldg4(cf + (CL::S + c) * PL), Ac = ldg4(cf + (CL::A + c) * PL);
+    const float* row = sr + c * SRC;
+    const F4 pc = lds4(row);
+    u[c] = mul4(Ac, fma4(Sc, pc, u[c]));  // u_c = A_c (S_c p_rc + P_c)
+    F4 q = fma4(Sc, u[c], mul4(ldg4(cf + CL::DR * PL), pc));
+    {
+      const F4 eR = ldg4(cf + CL::WR * PL), eD = ldg4(cf + CL::WD * PL);
+      const F4 eL = f4v(eLm, eR.a.x, eR.a.y, eR.b.x);
+      const F4 right = f4v(pc.a.y, pc.b.x, pc.b.y, row[4]);
+      const F4 left = f4v(row[-1], pc.a.x, pc.a.y, pc.b.x);
+      q = fma4(eR, sub4(pc, right), q);
+      q = fma4(eL, sub4(pc, left), q);
+      q = fma4(eD, sub4(pc, lds4(row + SRR)), q);
+      if (hU) q = fma4(ldg4(cf + CL::WD * PL - P.pitch), sub4(pc, lds4(row - SRR)), q);
+    }
+#pragma unroll
+    for (int j = 0; j < GID_MAX_PAIRS; j++) {
+      if (j < P.ns) {
+        const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
+        const float* fw = row + dy * SRR + dx;
+        const float* bw = row - dy * SRR - dx;
+        q = fma4(ldg4(cf + (CL::CW + j) * PL), sub4(pc, f4v(fw[0], fw[1], fw[2], fw[3])), q);
+        q = fma4(ldg4(cf + (CL::CW + P.ns + j) * PL), sub4(pc, f4v(bw[0], bw[1], bw[2], bw[3])), q);
+      }
+    }
+    finish(c, pc, mul4(q, valid));
+  }
+  // monochrome block: M_c = w_m sum_k dm_kc p_Tk
+  F4 Mc[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) Mc[c] = f4s(0.f);
+#pragma unroll
+  for (int k = 0; k <= K; k++) {
+    const F4 pk = lds4(st + k * STC);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Mc[c] = fma4(f4s(ct.dm[k][c]), pk, Mc[c]);
+  }
+  {
+    const F4 wm = ldg4(cf + CL::WM * PL);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
+  }
+  // layers: data and monochrome back-projections, diagonal IRLS weights, smoothness
+#pragma unroll(ROLL ? 1 : K + 1)
+  for (int k = 0; k <= K; k++) {
+    const float* row = st + k * STC;
+    const F4 pk = lds4(row);
+    const F4 sR = ldg4(cf + (CL::ER + k) * PL), sD = ldg4(cf + (CL::ED + k) * PL);
+    float sLm;
+    if constexpr (SHFL) {
+      const float sh = __shfl_up_sync(0xffffffffu, sR.b.y, 1);
+      sLm = left_lane ? sh : (hL ? cf[(CL::ER + k) * PL - 1] : 0.f);
+    } else {
+      sLm = hL ? cf[(CL::ER + k) * PL - 1] : 0.f;
+    }
+    const F4 sL = f4v(sLm, sR.a.x, sR.a.y, sR.b.x);
+    const F4 sU = hU ? ldg4(cf + (CL::ED + k) * PL - P.pitch) : f4s(0.f);
+    const F4 right = f4v(pk.a.y, pk.b.x, pk.b.y, row[4]);
+    const F4 left = f4v(row[-1], pk.a.x, pk.a.y, pk.b.x);
+    const F4 down = lds4(row + STR), up = lds4(row - STR);
+    F4 q = mul4(ldg4(cf + (CL::WT + k) * PL), pk);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      q = fma4(f4s(ct.b[k][c]), u[c], q);
+      q = fma4(f4s(ct.dm[k][c]), Mc[c], q);
+    }
+    q = fma4(sR, sub4(pk, right), q);
+    q = fma4(sL, sub4(pk, left), q);
+    q = fma4(sD, sub4(pk, down), q);
+    q = fma4(sU, sub4(pk, up), q);
+    finish(3 + k, pk, mul4(q, valid));
+  }
+}
 
 // PCG operator step it: p = z + beta p_old (first step: p = z), q = J^T J p
 // from the step's coefficient planes, block partials of <p, q>.  The
@@ -839,7 +969,6 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
                                             int mode, int first, GB get_beta, const float* pin, float* pout,
                                             float* __restrict__ qout, const CUtensorMap* mapR = nullptr,
                                             const CUtensorMap* mapT = nullptr) {
-  using CL = CoefLayout<K>;
   constexpr int NCH = VRW / 4;  // float4 chunks per staged row
   constexpr int NTH = BX * TH;  // threads per block
   const int tid = tid_flat();
@@ -875,7 +1004,14 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
     }
     bool done = false;
     for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
-    if (!done && tid == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+    if (!__syncthreads_and(done)) {
+      // the copy did not complete in time: record it, give the copy still in
+      // flight into this block's shared memory a second bounded wait, and leave
+      // p and q unwritten (the status makes the next synchronising call fail)
+      if (tid == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+      for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
+      return 0.f;
+    }
   } else {
     // Every chunk is an asynchronous 16-byte copy straight into shared memory
     // (zero-filled outside the frame): all of a thread's copies are in flight
@@ -894,10 +1030,7 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
   const int y = y0 + threadIdx.y, x = x0 + QW * threadIdx.x;
   if (x < P.W && y < P.H) {
     const long o = off2(P, y, x);
-    const float* __restrict__ cf = P.coef + o;
     const long PL = P.plane;
-    const bool hL = x > 0, hU = y > 0;
-    const F4 valid = f4v(1.f, x + 1 < P.W ? 1.f : 0.f, x + 2 < P.W ? 1.f : 0.f, x + 3 < P.W ? 1.f : 0.f);
     // q = A s on the valid pixels; in a PCG step p = z + beta p_old and, A being
     // fixed within the Gauss-Newton step, q = A p = A z + beta q_old.
     const F4 bb = f4s(beta);
@@ -905,8 +1038,8 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
     // staged tile reads zero outside the frame, so q and p stay zero there (the
     // first step of every Gauss-Newton step rewrites them from z, whose padding
     // k_linearize has just zeroed).
-    auto finish = [&](int v, F4 s, F4 as) {
-      F4 q = mul4(as, valid), p = s;
+    auto finish = [&](int v, F4 s, F4 q) {
+      F4 p = s;
       const long ov = v * PL + o;
       if (mode == 0 && !first) {
         p = fma4(bb, ldg4(pin + ov), s);
@@ -917,89 +1050,8 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
       pq += dot4(p, q);
     };
     const int cx = VHX + QW * threadIdx.x, ry = threadIdx.y + AHR, ty = threadIdx.y + 1;
-    // data block: P_c = sum_k b_kc p_Tk
-    F4 u[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) u[c] = f4s(0.f);
-#pragma unroll
-    for (int k = 0; k <= K; k++) {
-      const F4 pk = lds4(&t.pt[k][ty][cx]);
-#pragma unroll
-      for (int c = 0; c < 3; c++) u[c] = fma4(f4s(ct.b[k][c]), pk, u[c]);
-    }
-    // reflectance channels, one at a time: data, clustering/temporal diagonal,
-    // r-sparsity, consistency pairs (x, x + o_j) and (x - o_j, x); the shared
-    // per-pixel weights are re-read through L1 rather than held in registers
-    const float eLm = hL ? cf[CL::WR * PL - 1] : 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; c++) {
-      const F4 Sc = ldg4(cf + (CL::S + c) * PL), Ac = ldg4(cf + (CL::A + c) * PL);
-      const float* row = &t.pr[c][ry][cx];
-      const F4 pc = lds4(row);
-      u[c] = mul4(Ac, fma4(Sc, pc, u[c]));  // u_c = A_c (S_c p_rc + P_c)
-      F4 q = fma4(Sc, u[c], mul4(ldg4(cf + CL::DR * PL), pc));
-      {
-        const F4 eR = ldg4(cf + CL::WR * PL), eD = ldg4(cf + CL::WD * PL);
-        const F4 eL = f4v(eLm, eR.a.x, eR.a.y, eR.b.x);
-        const F4 right = f4v(pc.a.y, pc.b.x, pc.b.y, row[4]);
-        const F4 left = f4v(row[-1], pc.a.x, pc.a.y, pc.b.x);
-        q = fma4(eR, sub4(pc, right), q);
-        q = fma4(eL, sub4(pc, left), q);
-        q = fma4(eD, sub4(pc, lds4(&t.pr[c][ry + 1][cx])), q);
-        if (hU) q = fma4(ldg4(cf + CL::WD * PL - P.pitch), sub4(pc, lds4(&t.pr[c][ry - 1][cx])), q);
-      }
-#pragma unroll
-      for (int j = 0; j < GID_MAX_PAIRS; j++) {
-        if (j < P.ns) {
-          const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
-          const float* fw = &t.pr[c][ry + dy][cx + dx];
-          const float* bw = &t.pr[c][ry - dy][cx - dx];
-          q = fma4(ldg4(cf + (CL::CW + j) * PL), sub4(pc, f4v(fw[0], fw[1], fw[2], fw[3])), q);
-          q = fma4(ldg4(cf + (CL::CW + P.ns + j) * PL), sub4(pc, f4v(bw[0], bw[1], bw[2], bw[3])), q);
-        }
-      }
-      finish(c, pc, q);
-    }
-    // monochrome block: M_c = w_m sum_k dm_kc p_Tk
-    F4 Mc[3];
-#pragma unroll
-    for (int c = 0; c < 3; c++) Mc[c] = f4s(0.f);
-#pragma unroll
-    for (int k = 0; k <= K; k++) {
-      const F4 pk = lds4(&t.pt[k][ty][cx]);
-#pragma unroll
-      for (int c = 0; c < 3; c++) Mc[c] = fma4(f4s(ct.dm[k][c]), pk, Mc[c]);
-    }
-    {
-      const F4 wm = ldg4(cf + CL::WM * PL);
-#pragma unroll
-      for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
-    }
-    // layers: data and monochrome back-projections, diagonal IRLS weights, smoothness
-    // (not unrolled for the one-wave tile: its register budget is 96 per thread)
-#pragma unroll(TH >= 17 ? 1 : K + 1)
-    for (int k = 0; k <= K; k++) {
-      const float* row = &t.pt[k][ty][cx];
-      const F4 pk = lds4(row);
-      const F4 sR = ldg4(cf + (CL::ER + k) * PL), sD = ldg4(cf + (CL::ED + k) * PL);
-      const float sLm = hL ? cf[(CL::ER + k) * PL - 1] : 0.f;
-      const F4 sL = f4v(sLm, sR.a.x, sR.a.y, sR.b.x);
-      const F4 sU = hU ? ldg4(cf + (CL::ED + k) * PL - P.pitch) : f4s(0.f);
-      const F4 right = f4v(pk.a.y, pk.b.x, pk.b.y, row[4]);
-      const F4 left = f4v(row[-1], pk.a.x, pk.a.y, pk.b.x);
-      const F4 down = lds4(&t.pt[k][ty + 1][cx]), up = lds4(&t.pt[k][ty - 1][cx]);
-      F4 q = mul4(ldg4(cf + (CL::WT + k) * PL), pk);
-#pragma unroll
-      for (int c = 0; c < 3; c++) {
-        q = fma4(f4s(ct.b[k][c]), u[c], q);
-        q = fma4(f4s(ct.dm[k][c]), Mc[c], q);
-      }
-      q = fma4(sR, sub4(pk, right), q);
-      q = fma4(sL, sub4(pk, left), q);
-      q = fma4(sD, sub4(pk, down), q);
-      q = fma4(sU, sub4(pk, up), q);
-      finish(3 + k, pk, q);
-    }
+    op_apply4<K, TH >= 17>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
+                           VRW, finish);
   }
   return pq;
 }
@@ -1501,6 +1553,553 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     rho_old = rho;
     rho = block_total(part_share(part_rz, nb));
     if (b == 0 && tid == 0 && m < PCG_HIST) P.sc->rho_hist[m] = rho;
+  }
+}
+
+// ---------------------------------------------------------------- resident PCG
+
+// All M PCG steps of one Gauss-Newton step in one cooperative launch whose
+// blocks keep their share of the PCG state on chip for the whole step, with one
+// grid-wide synchronisation per PCG step.  Block b owns one tile of 4 TX x TH
+// pixels (tile column b % ntx, tile row b / ntx; thread tid < TX x TH owns the
+// four pixels 4 tx .. 4 tx + 3 of the tile's row ty, tx = tid % TX, ty = tid /
+// TX) and holds in shared memory
+//   ring [RES_NSLOT] slots   coefficient planes of the tile, see below
+//   zr  [3][TH + 6][RW]      z of the reflectance channels with a 3-row, 4-column halo
+//   zt  [K + 1][TH + 2][RW]  z of the layers with a 1-row, 4-column halo   (RW = 4 TX + 8)
+//   ps  [V][TH][4 TX]        p at the tile's pixels
+// while M^-1 q (written mq), delta and M^-1 stream from global memory.  The
+// operator coefficients stream through the ring: the block's last warp (the
+// producer) copies one plane at a time (rows y0 - 1 .. y0 + TH - 1, columns
+// x0 - 4 .. x0 + 4 TX + 3: the row above and the column to the left carry the
+// up and left edge weights) with TMA into the next free slot, in the order the
+// arithmetic consumes them (res_plane), and runs ahead into the next PCG step
+// while the block synchronises; every other warp consumes each plane once and
+// frees its slot.  PCG step m (z, p, beta and rho = <r, z> known):
+//   operator phase: p = z + beta p, q = J^T J z + beta q (the q recurrence of
+//     k_apply; q_old = mq_old / M^-1), mq = M^-1 q; block partials of <p, q>,
+//     <z, q> and <q, M^-1 q>; the tile's border rows and columns of mq (the
+//     part its neighbours' halos need) go to the exchange planes zx;
+//   grid all-reduce of the three partials; every block forms alpha = rho /
+//     <p, q> and rho' = <r', z'> = rho - 2 alpha <z, q> + alpha^2 <q, M^-1 q>
+//     (r' = r - alpha q, z' = z - alpha M^-1 q, and <r, M^-1 q> = <z, q>: the
+//     expansion is exact in exact arithmetic), beta' = rho' / rho;
+//   vector phase: delta += alpha p, z -= alpha mq on the tile's pixels, and on
+//     its halo from the neighbours' published mq, by the same fused
+//     multiply-add, so that every block's halo copy stays equal bit for bit to
+//     the value its owner holds.
+// Textbook PCG needs a second grid-wide step per PCG step (rho' after z'); this
+// recurrence needs one.  The operator's arithmetic, in each plane's order, is
+// that of op_apply4; the sums differ from the two-kernel loop's in the grouping
+// of the FP32 partials and in rho', which is assembled from the three FP64
+// totals instead of summed from the updated z.
+struct ResTile {
+  int TX, TH, ntx, RW;
+};
+
+constexpr int RES_NSLOT = 4;    // coefficient ring slots
+constexpr int RES_MAXT = 576;   // threads per block at most (18 warps: a register budget of 96)
+__host__ __device__ constexpr long res_slot_bytes(int TX, int TH) {
+  return ((long)(4 * TX + 8) * (TH + 1) * 4 + 127) / 128 * 128;
+}
+__host__ __device__ constexpr long res_smem_bytes(int K, int TX, int TH) {
+  return 128 + RES_NSLOT * res_slot_bytes(TX, TH) +
+         4L * (3L * (TH + 6) * (4 * TX + 8) + (long)(K + 1) * (TH + 2) * (4 * TX + 8) + (long)(K + 4) * TH * (4 * TX));
+}
+// threads of a resident block: the owners rounded up to whole warps, plus the producer warp
+__host__ __device__ constexpr int res_threads(int TX, int TH) { return (TX * TH + 31) / 32 * 32 + 32; }
+
+// Coefficient plane (CoefLayout index) consumed i-th by the resident operator:
+// DR, then S_c, A_c for c = 0..2, WR, WD, the consistency pairs (forward,
+// backward) j < ns, WM, then WT_k, ER_k, ED_k for k = 0..K.
+template <int K>
+__device__ __forceinline__ int res_plane(int i, int ns) {
+  using CL = CoefLayout<K>;
+  if (i == 0) return CL::DR;
+  if (i <= 6) return ((i - 1) & 1) ? CL::A + (i - 1) / 2 : CL::S + (i - 1) / 2;
+  if (i == 7) return CL::WR;
+  if (i == 8) return CL::WD;
+  if (i < 9 + 2 * ns) return CL::CW + (((i - 9) & 1) ? ns : 0) + (i - 9) / 2;
+  if (i == 9 + 2 * ns) return CL::WM;
+  const int r = i - 10 - 2 * ns, k = r / 3, t = r - 3 * k;
+  return t == 0 ? CL::WT + k : (t == 1 ? CL::ER + k : CL::ED + k);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+// bounded wait on an mbarrier phase; false (and ST_TIMEOUT recorded) if it ran out
+__device__ __forceinline__ bool mbar_wait_bounded(const Params& P, uint64_t* bar, unsigned parity) {
+  for (long i = 0; i < TMA_SPINS; i++)
+    if (mbar_try_wait(bar, parity)) return true;
+  atomicOr(&P.sc->status, ST_TIMEOUT);
+  return false;
+}
+
+// q = A s at one thread's four pixels, as op_apply4, with every coefficient
+// read from the ring: wait(i) waits for the i-th plane of the sequence and
+// returns its slot's element at the thread's first pixel (row stride SW; the
+// slot holds the row above and the columns to the left), done(i) frees it.
+// The reflectance channels are accumulated side by side, so that each shared
+// plane is read once; each channel's operations keep op_apply4's order.
+template <int K, class WAIT, class DONE, class FIN>
+__device__ __forceinline__ void op_ring4(const Params& P, const ColorTable<K>& ct, int x, const float* sr, int SRC,
+                                         int SRR, const float* st, int STC, int STR, int SW, WAIT wait, DONE done,
+                                         FIN finish) {
+  const F4 valid = f4v(1.f, x + 1 < P.W ? 1.f : 0.f, x + 2 < P.W ? 1.f : 0.f, x + 3 < P.W ? 1.f : 0.f);
+  F4 u[3], pc[3], q[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) {
+    u[c] = f4s(0.f);
+    pc[c] = lds4(sr + c * SRC);
+  }
+#pragma unroll
+  for (int k = 0; k <= K; k++) {
+    const F4 pk = lds4(st + k * STC);
+#pragma unroll
+    for (int c = 0; c < 3; c++) u[c] = fma4(f4s(ct.b[k][c]), pk, u[c]);
+  }
+  int i = 0;
+  {  // clustering + temporal diagonal
+    const F4 dr = lds4(wait(i));
+    done(i++);
+#pragma unroll
+    for (int c = 0; c < 3; c++) q[c] = mul4(dr, pc[c]);
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) {  // data term: u_c = A_c (S_c p_rc + P_c), q_c += S_c u_c
+    const F4 Sc = lds4(wait(i));
+    done(i++);
+    const F4 Ac = lds4(wait(i));
+    done(i++);
+    u[c] = mul4(Ac, fma4(Sc, pc[c], u[c]));
+    q[c] = fma4(Sc, u[c], q[c]);
+  }
+  {  // r-sparsity: right and left edges, then down and up
+    const float* w = wait(i);
+    const F4 eR = lds4(w), eL = f4v(w[-1], eR.a.x, eR.a.y, eR.b.x);
+    done(i++);
+    const float* wd = wait(i);
+    const F4 eD = lds4(wd), eU = lds4(wd - SW);
+    done(i++);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      const float* row = sr + c * SRC;
+      const F4 right = f4v(pc[c].a.y, pc[c].b.x, pc[c].b.y, row[4]);
+      const F4 left = f4v(row[-1], pc[c].a.x, pc[c].a.y, pc[c].b.x);
+      q[c] = fma4(eR, sub4(pc[c], right), q[c]);
+      q[c] = fma4(eL, sub4(pc[c], left), q[c]);
+      q[c] = fma4(eD, sub4(pc[c], lds4(row + SRR)), q[c]);
+      q[c] = fma4(eU, sub4(pc[c], lds4(row - SRR)), q[c]);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < GID_MAX_PAIRS; j++) {  // consistency pairs (x, x + o_j) and (x - o_j, x)
+    if (j < P.ns) {
+      const int dy = P.off_s[2 * j], dx = P.off_s[2 * j + 1];
+      const F4 wf = lds4(wait(i));
+      done(i++);
+      const F4 wb = lds4(wait(i));
+      done(i++);
+#pragma unroll
+      for (int c = 0; c < 3; c++) {
+        const float* fw = sr + c * SRC + dy * SRR + dx;
+        const float* bw = sr + c * SRC - dy * SRR - dx;
+        q[c] = fma4(wf, sub4(pc[c], f4v(fw[0], fw[1], fw[2], fw[3])), q[c]);
+        q[c] = fma4(wb, sub4(pc[c], f4v(bw[0], bw[1], bw[2], bw[3])), q[c]);
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < 3; c++) finish(c, pc[c], mul4(q[c], valid));
+  // monochrome block: M_c = w_m sum_k dm_kc p_Tk
+  F4 Mc[3];
+#pragma unroll
+  for (int c = 0; c < 3; c++) Mc[c] = f4s(0.f);
+#pragma unroll
+  for (int k = 0; k <= K; k++) {
+    const F4 pk = lds4(st + k * STC);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Mc[c] = fma4(f4s(ct.dm[k][c]), pk, Mc[c]);
+  }
+  {
+    const F4 wm = lds4(wait(i));
+    done(i++);
+#pragma unroll
+    for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
+  }
+  // layers: diagonal IRLS weights, data and monochrome back-projections, smoothness
+#pragma unroll 1
+  for (int k = 0; k <= K; k++) {
+    const float* row = st + k * STC;
+    const F4 pk = lds4(row);
+    const F4 wt = lds4(wait(i));
+    done(i++);
+    const float* er = wait(i);
+    const F4 sR = lds4(er), sL = f4v(er[-1], sR.a.x, sR.a.y, sR.b.x);
+    done(i++);
+    const float* ed = wait(i);
+    const F4 sD = lds4(ed), sU = lds4(ed - SW);
+    done(i++);
+    const F4 right = f4v(pk.a.y, pk.b.x, pk.b.y, row[4]);
+    const F4 left = f4v(row[-1], pk.a.x, pk.a.y, pk.b.x);
+    const F4 down = lds4(row + STR), up = lds4(row - STR);
+    F4 qk = mul4(wt, pk);
+#pragma unroll
+    for (int c = 0; c < 3; c++) {
+      qk = fma4(f4s(ct.b[k][c]), u[c], qk);
+      qk = fma4(f4s(ct.dm[k][c]), Mc[c], qk);
+    }
+    qk = fma4(sR, sub4(pk, right), qk);
+    qk = fma4(sL, sub4(pk, left), qk);
+    qk = fma4(sD, sub4(pk, down), qk);
+    qk = fma4(sU, sub4(pk, up), qk);
+    finish(3 + k, pk, mul4(qk, valid));
+  }
+}
+
+__device__ __forceinline__ unsigned ld_relaxed_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.relaxed.gpu.global.u32 %0, [%1];\n" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void red_release_add(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;\n" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ double* res_slot(const Params& P, unsigned n, int j) {
+  return P.xval + ((long)(n % RES_ROWS) * RES_NV + j) * RES_MAXB;
+}
+__device__ __forceinline__ unsigned* res_count(const Params& P, unsigned n) {
+  return reinterpret_cast<unsigned*>(P.xval + (long)RES_ROWS * RES_NV * RES_MAXB) + 32 * (n % RES_ROWS);
+}
+
+// Block sums of three per-thread FP32 partials (as block_sum_f, one pass):
+// valid in thread 0.
+__device__ __forceinline__ void block_sum3_f(float a, float b, float c, double (&out)[RES_NV]) {
+  __shared__ float sh[32][RES_NV];
+  const int t = tid_flat(), lane = t & 31, wid = t >> 5;
+  const int nw = (blockDim.x * blockDim.y + 31) >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    a += __shfl_down_sync(0xffffffffu, a, o);
+    b += __shfl_down_sync(0xffffffffu, b, o);
+    c += __shfl_down_sync(0xffffffffu, c, o);
+  }
+  if (lane == 0) {
+    sh[wid][0] = a;
+    sh[wid][1] = b;
+    sh[wid][2] = c;
+  }
+  __syncthreads();
+  if (wid == 0)
+#pragma unroll
+    for (int j = 0; j < RES_NV; j++) out[j] = warp_tree(lane < nw ? (double)sh[lane][j] : 0.0);
+}
+
+// Grid all-reduce number n (1, 2, ... within the launch) of the resident
+// kernel.  part[j] (valid in thread 0) are the block's FP64 partials.  Thread 0
+// of block b stores them in its slots of row n % RES_ROWS and adds one to that
+// row's arrival counter with release semantics (which also publishes the
+// block's earlier global writes: the border mq its neighbours read); it then
+// polls the counter (relaxed loads, at most the injected or default poll
+// limit) until every block has arrived, and fences.  Every block then reads
+// all slots and sums them in the same fixed order, so all blocks hold the same
+// totals.  Block 0 clears the counter of row n - 1, which every block has
+// finished polling (they all arrived here); it is reused at synchronisation
+// n - 1 + RES_ROWS, after the clear is visible to every block (they pass
+// synchronisation n + 1 on the way).  The counters start at zero: k_linearize,
+// the kernel before every launch, clears them.  False (and ST_TIMEOUT
+// recorded) if the wait ran out; all threads of the block agree.
+__device__ __forceinline__ bool res_allreduce(const Params& P, unsigned n, const double (&part)[RES_NV],
+                                              double (&total)[RES_NV]) {
+  const int tid = tid_flat(), nb = gridDim.x;
+  bool late = false;
+  if (tid == 0) {
+#pragma unroll
+    for (int j = 0; j < RES_NV; j++) res_slot(P, n, j)[blockIdx.x] = part[j];
+    unsigned* cnt = res_count(P, n);
+    red_release_add(cnt, 1u);
+    const unsigned want = (unsigned)min(nb + (int)P.sc->phantom, RES_MAXB + 1);
+    const long long limit = P.sc->spin_limit > 0 ? P.sc->spin_limit : GRID_SPINS;
+    bool ok = false;
+    for (long long s = 0; s < limit && !ok; s++) ok = ld_relaxed_u32(cnt) >= want;
+    late = !ok;
+    __threadfence();  // with the polls above: acquires every block's writes
+  }
+  if (__syncthreads_or(late)) {
+    if (tid == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+    return false;
+  }
+  if (tid == 0 && blockIdx.x == 0 && n > 1) *res_count(P, n - 1) = 0u;
+  __shared__ double tot[RES_NV];
+  if (tid < 32) {
+#pragma unroll
+    for (int j = 0; j < RES_NV; j++) {
+      const double s = warp_tree(part_share(res_slot(P, n, j), nb));
+      if (tid == 0) tot[j] = s;
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < RES_NV; j++) total[j] = tot[j];
+  return true;
+}
+
+template <int K>
+__global__ void __launch_bounds__(RES_MAXT, 1)
+    k_pcg_resident(Params P, ResTile g, int m_inner, int last_mode, float* __restrict__ mqg,
+                   const __grid_constant__ CUtensorMap mapC) {
+  constexpr int V = K + 4;
+  extern __shared__ __align__(128) float res_smem[];
+  __shared__ ColorTable<K> ct;
+  __shared__ __align__(8) uint64_t full[RES_NSLOT], empty[RES_NSLOT];
+  const int TX = g.TX, TH = g.TH, RW = g.RW, TW = 4 * TX, RR = TH + 6, TR = TH + 2, C4 = RW / 4;
+  const int SLOT = (int)(res_slot_bytes(TX, TH) / 4);  // floats per ring slot (row stride RW)
+  // the ring's slots are TMA destinations: 128-byte aligned (128 bytes of slack are allocated)
+  float* ring = reinterpret_cast<float*>((reinterpret_cast<uintptr_t>(res_smem) + 127) & ~uintptr_t(127));
+  float* zr = ring + RES_NSLOT * SLOT;
+  float* zt = zr + 3 * RR * RW;
+  float* ps = zt + (K + 1) * TR * RW;
+  load_colors<K>(ct, P.col);
+  const int tid = threadIdx.x, nth = blockDim.x, tx = tid % TX, ty = tid / TX;
+  const int nown = (TX * TH + 31) / 32;  // consumer warps; warp nown is the producer
+  const bool producer = tid == nown * 32;
+  const int x0 = (blockIdx.x % g.ntx) * TW, y0 = (blockIdx.x / g.ntx) * TH;
+  const int x = x0 + 4 * tx, y = y0 + ty;
+  const bool consumer = tid < nown * 32;
+  const bool own = ty < TH && x < P.W && y < P.H;
+  const long PL = P.plane, o = own ? off2(P, y, x) : 0;
+  const long zxs = (long)V * PL;  // the exchange planes are double-buffered by step parity
+  const int NCP = coef_planes(K, P.ns);
+  const unsigned box_bytes = (unsigned)((TW + 8) * (TH + 1) * 4);
+  if (tid == 0) {
+    for (int s = 0; s < RES_NSLOT; s++) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], nown);
+    }
+  }
+  __syncthreads();
+  // the producer's copies: sequence plane gi (over the launch) into slot gi % RES_NSLOT
+  long issued = 0;
+  auto produce = [&](long upto) {
+    for (; issued < upto; issued++) {
+      const int s = (int)(issued % RES_NSLOT);
+      const long use = issued / RES_NSLOT;
+      if (use > 0) mbar_wait_bounded(P, &empty[s], (unsigned)((use - 1) & 1));
+      mbar_expect_tx(&full[s], box_bytes);
+      tma_load_3d(ring + s * SLOT, &mapC, x0 - 4, y0 - 1, res_plane<K>((int)(issued % NCP), P.ns), &full[s]);
+    }
+  };
+  // staged chunk (plane v, staged row ly, float4 column lc): shared address and
+  // frame position (gy, gx); in_frame: inside the frame's rows and pitch (the
+  // pitch's padding columns are zero in every plane)
+  auto chunk = [&](int v, int ly, int lc, int& gy, int& gx) -> float* {
+    gy = y0 - (v < 3 ? 3 : 1) + ly;
+    gx = x0 - 4 + 4 * lc;
+    return v < 3 ? zr + (v * RR + ly) * RW + 4 * lc : zt + ((v - 3) * TR + ly) * RW + 4 * lc;
+  };
+  auto in_frame = [&](int gy, int gx) { return gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch; };
+  // prologue: the whole staged tile of z from the PCG start; the producer
+  // starts the coefficient ring meanwhile
+  if (producer) produce(min((long)RES_NSLOT, (long)NCP * m_inner));
+  {
+    const int nr = 3 * RR * C4, ntot = nr + (K + 1) * TR * C4;
+    for (int i = tid; i < ntot; i += nth) {
+      int v, r, gy, gx;
+      if (i < nr) {
+        v = i / (RR * C4);
+        r = i - v * RR * C4;
+      } else {
+        const int k = (i - nr) / (TR * C4);
+        v = 3 + k;
+        r = i - nr - k * TR * C4;
+      }
+      float* dst = chunk(v, r / C4, r % C4, gy, gx);
+      const bool in = in_frame(gy, gx);
+      cp_async16(dst, in ? P.z + v * PL + off2(P, gy, gx) : P.z, in ? 16 : 0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  }
+  // halo chunk i: per reflectance channel the 3 rows above and below (full
+  // width) and the 4 columns left and right of the tile's rows; per layer 1 row
+  // and the same columns
+  const int HR = 6 * C4 + 2 * TH, HT = 2 * C4 + 2 * TH, nhalo = 3 * HR + (K + 1) * HT;
+  auto halo = [&](int i, int& v, int& gy, int& gx) -> float* {
+    int ly, lc, j;
+    if (i < 3 * HR) {
+      v = i / HR;
+      j = i - v * HR;
+      if (j < 6 * C4) {
+        const int r = j / C4;
+        ly = r < 3 ? r : TH + r;
+        lc = j - r * C4;
+      } else {
+        j -= 6 * C4;
+        ly = 3 + (j >> 1);
+        lc = (j & 1) ? C4 - 1 : 0;
+      }
+    } else {
+      const int k = (i - 3 * HR) / HT;
+      v = 3 + k;
+      j = i - 3 * HR - k * HT;
+      if (j < 2 * C4) {
+        const int r = j / C4;
+        ly = r == 0 ? 0 : TH + 1;
+        lc = j - r * C4;
+      } else {
+        j -= 2 * C4;
+        ly = 1 + (j >> 1);
+        lc = (j & 1) ? C4 - 1 : 0;
+      }
+    }
+    return chunk(v, ly, lc, gy, gx);
+  };
+  // this thread's chunk is part of a neighbour's halo (reflectance / layers)
+  const bool edge_x = tx == 0 || tx == TX - 1;
+  const bool pub_r = edge_x || ty < 3 || ty >= TH - 3, pub_t = edge_x || ty == 0 || ty == TH - 1;
+  const int oy = own ? ty : 0, ox = own ? tx : 0;  // (threads that own no chunk compute on chunk 0 and discard it)
+  float* sr = zr + (oy + 3) * RW + 4 + 4 * ox;
+  float* st = zt + (oy + 1) * RW + 4 + 4 * ox;
+  float* pp = ps + oy * TW + 4 * ox;
+  const int sown = (oy + 1) * RW + 4 + 4 * ox;  // the thread's first pixel in a ring slot
+  auto zs = [&](int v) -> float* { return v < 3 ? sr + v * RR * RW : st + (v - 3) * TR * RW; };
+  double rho = P.sc->rho;
+  float beta = 0.f;
+  long consumed = 0;  // ring sequence position of this step's first plane
+  for (int m = 1; m <= m_inner; m++) {
+    const int first = m == 1;
+    float* zx = P.zx + (m & 1) * zxs;
+    // operator phase
+    float pq = 0.f, zq = 0.f, qmq = 0.f;
+    if (consumer) {
+      const F4 bb = f4s(beta);
+      auto wait = [&](int i) -> const float* {
+        const long gi = consumed + i;
+        const int s = (int)(gi % RES_NSLOT);
+        mbar_wait_bounded(P, &full[s], (unsigned)((gi / RES_NSLOT) & 1));
+        return ring + s * SLOT + sown;
+      };
+      auto done = [&](int i) {
+        __syncwarp();
+        if ((tid & 31) == 0) mbar_arrive(&empty[(int)((consumed + i) % RES_NSLOT)]);
+      };
+      auto finish = [&](int v, F4 s, F4 q) {
+        if (!own) return;
+        F4 p = s;
+        const long ov = v * PL + o;
+        float* pv = pp + v * TH * TW;
+        const F4 mi = ldc4(P.Minv + ov);
+        if (!first) {
+          // q_old = mq_old / M^-1 (padding lanes: M^-1 = 0, q_old = 0)
+          const float4 mo = __ldcg(reinterpret_cast<const float4*>(mqg + ov));
+          const F4 qo = f4v(mi.a.x > 0.f ? __fdividef(mo.x, mi.a.x) : 0.f, mi.a.y > 0.f ? __fdividef(mo.y, mi.a.y) : 0.f,
+                            mi.b.x > 0.f ? __fdividef(mo.z, mi.b.x) : 0.f, mi.b.y > 0.f ? __fdividef(mo.w, mi.b.y) : 0.f);
+          p = fma4(bb, lds4(pv), s);
+          q = fma4(bb, qo, q);
+        }
+        const F4 mq = mul4(mi, q);
+        __stcg(reinterpret_cast<float4*>(mqg + ov), to4(mq));
+        if (v < 3 ? pub_r : pub_t) __stcg(reinterpret_cast<float4*>(zx + ov), to4(mq));
+        *reinterpret_cast<float4*>(pv) = to4(p);
+        pq += dot4(p, q);
+        zq += dot4(s, q);
+        qmq += dot4(q, mq);
+      };
+      op_ring4<K>(P, ct, own ? x : 0, sr, RR * RW, RW, st, TR * RW, RW, RW, wait, done, finish);
+    } else if (producer) {
+      // this step's planes, then the next step's first planes (copied while the
+      // block synchronises and runs the vector phase)
+      produce(min((long)NCP * m + RES_NSLOT, (long)NCP * m_inner));
+    }
+    consumed += NCP;
+    double part[RES_NV], tot[RES_NV];
+    block_sum3_f(pq, zq, qmq, part);
+    if (!res_allreduce(P, (unsigned)m, part, tot)) return;
+    const double ad = tot[0] != 0.0 ? rho / tot[0] : 0.0;
+    const double rho_new = rho - 2.0 * ad * tot[1] + ad * ad * tot[2];
+    const float alpha = (float)ad;
+    const int last = m == m_inner ? last_mode : 0;
+    // vector phase: the halo's loads first, then the tile's pixels, then the halo
+    constexpr int HB = 1;
+    float4 hmq[HB];
+    float* hz[HB];
+#pragma unroll
+    for (int u = 0; u < HB; u++) {
+      hz[u] = nullptr;
+      const int i = tid + u * nth;
+      if (!last && i < nhalo) {
+        int v, gy, gx;
+        float* zp = halo(i, v, gy, gx);
+        if (in_frame(gy, gx)) {
+          hz[u] = zp;
+          hmq[u] = __ldcg(reinterpret_cast<const float4*>(zx + v * PL + off2(P, gy, gx)));
+        }
+      }
+    }
+    if (own) {
+      // all loads of a pair of planes before their stores (a cache-hinted store
+      // is ordered before the loads that follow it)
+#pragma unroll 1
+      for (int v0 = 0; v0 < V; v0 += 2) {
+        float4 pv[2], dv[2], mv[2];
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int v = v0 + u;
+          if (v < V) {
+            const long ov = v * PL + o;
+            pv[u] = *reinterpret_cast<const float4*>(pp + v * TH * TW);
+            dv[u] = __ldcg(reinterpret_cast<const float4*>(P.d + ov));
+            if (!last) mv[u] = __ldcg(reinterpret_cast<const float4*>(mqg + ov));
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 2; u++) {
+          const int v = v0 + u;
+          if (v >= V) continue;
+          const long ov = v * PL + o;
+          const float4 p = pv[u], d = dv[u];
+          const float4 dn = make_float4(fmaf(alpha, p.x, d.x), fmaf(alpha, p.y, d.y), fmaf(alpha, p.z, d.z),
+                                        fmaf(alpha, p.w, d.w));
+          if (last == 1) {
+            float4* xv = reinterpret_cast<float4*>(P.X + ov);
+            const float4 xo = *xv;
+            *xv = make_float4(xo.x + dn.x, xo.y + dn.y, xo.z + dn.z, xo.w + dn.w);
+            continue;
+          }
+          __stcg(reinterpret_cast<float4*>(P.d + ov), dn);
+          if (last == 2) continue;
+          const float4 mq = mv[u];
+          float* zp = zs(v);
+          const float4 z = *reinterpret_cast<const float4*>(zp);
+          *reinterpret_cast<float4*>(zp) = make_float4(fmaf(-alpha, mq.x, z.x), fmaf(-alpha, mq.y, z.y),
+                                                       fmaf(-alpha, mq.z, z.z), fmaf(-alpha, mq.w, z.w));
+        }
+      }
+    }
+    if (last) break;
+    // the halo from the neighbours' published mq, by the owners' operation
+#pragma unroll
+    for (int u = 0; u < HB; u++) {
+      if (hz[u]) {
+        const float4 mq = hmq[u], z = *reinterpret_cast<const float4*>(hz[u]);
+        *reinterpret_cast<float4*>(hz[u]) = make_float4(fmaf(-alpha, mq.x, z.x), fmaf(-alpha, mq.y, z.y),
+                                                        fmaf(-alpha, mq.z, z.z), fmaf(-alpha, mq.w, z.w));
+      }
+    }
+    for (int i = tid + HB * nth; i < nhalo; i += nth) {
+      int v, gy, gx;
+      float* zp = halo(i, v, gy, gx);
+      if (!in_frame(gy, gx)) continue;
+      const float4 mq = __ldcg(reinterpret_cast<const float4*>(zx + v * PL + off2(P, gy, gx)));
+      const float4 z = *reinterpret_cast<const float4*>(zp);
+      *reinterpret_cast<float4*>(zp) = make_float4(fmaf(-alpha, mq.x, z.x), fmaf(-alpha, mq.y, z.y),
+                                                   fmaf(-alpha, mq.z, z.z), fmaf(-alpha, mq.w, z.w));
+    }
+    beta = rho != 0.0 ? (float)(rho_new / rho) : 0.f;
+    rho = rho_new;
+    if (blockIdx.x == 0 && tid == 0 && m < PCG_HIST) P.sc->rho_hist[m] = rho;
+    __syncthreads();
   }
 }
 

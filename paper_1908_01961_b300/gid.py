@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(HERE, "libgid.so")
 
 GID_OK = 0
 PRECOND_JACOBI, PRECOND_BLOCK = 0, 1
+RESIDENT = -1  # gid_set_apply_tile: the resident PCG loop (GID_PCG_RESIDENT)
 ERR_TIMEOUT, ERR_NUMERIC = -5, -6
 ENERGY_TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness",
                 "non_neg")
@@ -33,7 +34,8 @@ EXPORTS = (
     "gid_get_base_colors", "gid_set_frame", "gid_init", "gid_run", "gid_get_layers", "gid_get_state",
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
-    "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_autotune",
+    "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_get_pcg_layout",
+    "gid_autotune",
     "gid_set_preconditioner", "gid_get_preconditioner", "gid_debug_inject", "gid_pcg_history",
     "gid_set_pcg_history",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
@@ -103,6 +105,7 @@ def load():
     L.gid_profile.argtypes = [P, I]
     L.gid_profile_read.argtypes = [P, D, LL]
     L.gid_set_apply_tile.argtypes = [P, I]
+    L.gid_get_pcg_layout.argtypes = [P] + [ctypes.POINTER(I)] * 4
     L.gid_set_preconditioner.argtypes = [P, I]
     L.gid_debug_inject.argtypes = [P, I, ctypes.c_longlong]
     L.gid_pcg_history.argtypes = [P, D, I, ctypes.POINTER(I)]
@@ -481,12 +484,19 @@ class Solver:
         return ("jacobi", "block")[self.lib.gid_get_preconditioner(self.h)]
 
     def autotune(self, reps: int = 10):
-        """Pick the fastest PCG execution (tile rows, 0 = persistent) on the current frame;
-        returns (rows, {rows: us per PCG step})."""
+        """Pick the fastest PCG execution (tile rows, 0 = persistent, -1 = resident) on the
+        current frame; returns (rows, {rows: us per PCG step})."""
         rows = ctypes.c_int()
-        us = (ctypes.c_float * 5)()
+        us = (ctypes.c_float * 6)()
         self._chk(self.lib.gid_autotune(self.h, reps, ctypes.byref(rows), us))
-        return rows.value, dict(zip((2, 4, 8, 17, 0), us[:]))
+        return rows.value, dict(zip((2, 4, 8, 17, 0, RESIDENT), us[:]))
+
+    def pcg_layout(self):
+        """(rows of the current PCG loop, (tile_w, tile_h, blocks) of the resident loop on this
+        frame, zeros if it does not fit) -- gid_get_pcg_layout."""
+        v = [ctypes.c_int() for _ in range(4)]
+        self._chk(self.lib.gid_get_pcg_layout(self.h, *[ctypes.byref(x) for x in v]))
+        return v[0].value, (v[1].value, v[2].value, v[3].value)
 
     # -- instrumentation
     def launch_count(self) -> int:
