@@ -49,8 +49,11 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the editing, clustering, correction and preconditioner measurements (profiling runs)")
-    ap.add_argument("--tile", type=int, default=None, choices=[0, 2, 4, 8, 17],
-                    help="operator tile rows instead of autotuning (0 = persistent PCG kernel); for profiling")
+    ap.add_argument("--tile", type=int, default=None, choices=[-1, 0, 2, 4, 8, 17],
+                    help="PCG loop instead of autotuning: operator tile rows, 0 = persistent kernel, "
+                         "-1 = resident kernel; for profiling")
+    ap.add_argument("--tile-cache", default=None,
+                    help="batch workload: file of autotuned tile shapes to read and extend (default: none)")
     ap.add_argument("--workload", default="video", choices=["video", "batch", "stream"],
                     help="video: the 640x480 K=6 video (default); batch: 24 uneven videos in one graph per step")
     return ap.parse_args()
@@ -125,9 +128,6 @@ class ClockSampler:
         self.f.flush()
         rows = [r.split(", ") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
         os.unlink(self.f.name)
-        if os.path.isdir(os.path.join(ROOT, "gpurun_out")):
-            with open(os.path.join(ROOT, "gpurun_out", "clocks.csv"), "w") as g:
-                g.write("\n".join(", ".join(r) for r in rows) + "\n")
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
         for r in rows:
@@ -191,23 +191,59 @@ def algorithmic_bytes(kind, K, P, M, ns, nt, temporal):
 
 # ---------------------------------------------------------------- reference arm (the oracle)
 
-def cpu_sample(seed=0):
-    """The FP64 oracle on one 640x480 frame, 1 of the 8 outer iterations (GN step
-    of 20 PCG + base-colour step), cold start; returns (seconds, frames/s)."""
+def cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+def host_threads():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_frame(threads, seed=0):
+    """The FP64 oracle's whole solve of frame 0 of the video (cold start, 8 outer
+    iterations of a Gauss-Newton step of 20 PCG steps and the base-colour step),
+    precompute included, on `threads` host threads (the oracle's loops are
+    spread by OpenMP; its results do not depend on the thread count).
+    Returns (seconds, X, b, energy history)."""
     import oracle as O
+    O.set_threads(threads)
     fr, b0 = make_video(seed, 1)
     off_s, _ = synth.offsets_for(seed)
     I = fr[0].I.astype(np.float32).astype(np.float64)
     t0 = time.perf_counter()
     C, wsr, om, _ = O.precompute(I, off_s)
     pb = O.Problem(I, fr[0].labels, b0.astype(np.float64), wsr, om, off_s)
-    O.solve_frame(pb, pb.init_cold(), 1, WORK["M"])
-    dt = time.perf_counter() - t0
-    return dt, 1.0 / (WORK["N"] * dt)
+    X, bo, hist = O.solve_frame(pb, pb.init_cold(), WORK["N"], WORK["M"])
+    return time.perf_counter() - t0, X, bo, hist
 
 
-CPU_SAMPLE = ("one 640x480 K=6 frame, 1 of its 8 outer iterations (precompute + GN step of 20 PCG + "
-              "base-colour step), FP64 oracle, 1 thread; frames/s = 1 / (8 x time)")
+CPU_SAMPLE = ("one whole 640x480 K=6 frame (frame 0 of the video: precompute, cold start, 8 x (GN step of 20 PCG "
+              "+ base-colour step)), FP64 oracle")
+
+
+def cpu_baseline():
+    """The oracle on the host: one whole frame on every host thread (the
+    reported value) and on one thread; returns (record, X, b, history) of the
+    all-thread run, whose result the parity block reuses."""
+    import oracle
+    oracle.build()
+    n = host_threads()
+    dt_n, X, bo, hist = oracle_frame(n)
+    dt_1, _, _, _ = oracle_frame(1)
+    rec = {"value": 1.0 / dt_n, "unit": "frames/s", "cores": n, "kind": "oracle", "sample": CPU_SAMPLE,
+           "seconds_per_frame": dt_n, "cores_1": {"cores": 1, "value": 1.0 / dt_1, "seconds_per_frame": dt_1},
+           "cores_nproc": {"cores": n, "value": 1.0 / dt_n, "seconds_per_frame": dt_n}, "cpu_model": cpu_model()}
+    return rec, X, bo, hist
 
 
 def run_reference(args, ws, rank):
@@ -215,19 +251,52 @@ def run_reference(args, ws, rank):
         return
     import oracle
     oracle.build()
+    n = host_threads()
     for _ in range(args.warmup):
-        cpu_sample(0)
-    times = [cpu_sample(0)[0] for _ in range(args.steps)]
+        oracle_frame(n)
+    times = [oracle_frame(n)[0] for _ in range(args.steps)]
     tot = sum(times)
-    value = args.steps / (WORK["N"] * tot)
+    value = args.steps / tot
     out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1000 * tot / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": WORKLOAD, "H": WORK["H"], "W": WORK["W"], "K": WORK["K"],
-                      "step": "1/8 of one frame (one outer iteration), scaled to frames/s"},
-           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE},
+                      "step": "one whole frame (frame 0: cold start, 8 x 20), on every host thread"},
+           "cpu_baseline": {"value": value, "unit": "frames/s", "cores": n, "kind": "oracle", "sample": CPU_SAMPLE,
+                            "cpu_model": cpu_model()},
            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
+
+
+def pcg_loop_name(s, rows):
+    if rows == -1:
+        _, (tw, th, nb) = s.pcg_layout()
+        return f"resident PCG kernel ({nb} tiles of {tw}x{th}, one per SM)"
+    if rows == 0:
+        return "persistent PCG kernel"
+    return f"128x{rows} operator tiles, operator and vector kernels per PCG step"
+
+
+def layer_errors(R, T, b, E, Xo, bo, Eo):
+    """Per-layer error of the GPU solve against the oracle's (max-abs and RMS of
+    R = exp(r) per channel set, T_0, each T_k, the base colours), the relative
+    energy error, and the non-negativity branch flips: layer values whose sign
+    (T > 0 or not, the branch of the non-negativity weight) differs."""
+    Ro, To = np.exp(Xo[:3]), Xo[3:]
+
+    def st(a, o):
+        d = np.asarray(a, np.float64) - np.asarray(o, np.float64)
+        return {"max_abs": float(np.abs(d).max()), "rms": float(np.sqrt(np.mean(d * d)))}
+
+    out = {"R": st(R, Ro), "T_0": st(T[0], To[0])}
+    for k in range(1, T.shape[0]):
+        out[f"T_{k}"] = st(T[k], To[k])
+    out["b"] = st(b, bo)
+    out["energy_rel"] = float(abs(E - Eo) / abs(Eo))
+    out["nonneg_branch_flips"] = int(np.count_nonzero((T > 0) != (To > 0)))
+    worst = max(v["max_abs"] for k, v in out.items() if isinstance(v, dict))
+    out["meets_bar"] = bool(worst <= 1e-3 and out["energy_rel"] <= 1e-4)
+    return out
 
 
 # ---------------------------------------------------------------- CUDA arm
@@ -300,30 +369,45 @@ def run_gid(args, ws, rank, local):
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms = kinds[dom][0] / kinds[dom][1]
-    alg = algorithmic_bytes(dom, K, P, M, len(off_s), len(off_t), True)
     peak, peak_src = measured_peaks()
     kernel_name = {"apply": "k_apply", "update": "k_update", "linearize": "k_linearize", "dense": "k_dense",
-                   "pcg": "k_pcg"}.get(dom)
-    traffic = ncu_traffic(kernel_name) if kernel_name else None
-    roof = None
-    if alg:
-        # The profiled step launches kernel by kernel with an event after each
-        # (no graph replay, no programmatic overlap), so it runs slower than the
-        # timed steps.  Per-launch time of the dominant kernel: its share of the
-        # profiled step times the timed step's own duration, over its launches;
-        # the raw profiled figure is reported beside it.
-        prof_total = sum(v[0] for v in kinds.values())
-        step_ms = total_ms / args.steps
-        dom_scaled = dom_ms * step_ms / prof_total
-        ach = alg / (dom_scaled / 1000.0) / 1e9
-        ach_prof = alg / (dom_ms / 1000.0) / 1e9
-        roof = {"bound": "hbm", "kernel": kernel_name, "achieved": ach, "peak": peak, "unit": "GB/s",
-                "frac": ach / peak, "traffic": traffic, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": alg, "avg_launch_ms": dom_scaled,
-                "avg_launch_ms_profiled": dom_ms, "frac_profiled": ach_prof / peak,
-                "method": "avg_launch_ms = (kernel's share of a profiled step with a CUDA event after every "
-                          "kernel) x (timed step duration) / launches; *_profiled = the profiled step's own "
-                          f"per-launch time (profiled step {prof_total:.1f} ms vs timed step {step_ms:.1f} ms)"}
+                   "pcg": "k_pcg_resident" if tile_rows == -1 else "k_pcg"}.get(dom)
+    # The profiled step launches kernel by kernel with an event after each (no
+    # graph replay, no programmatic overlap), so it runs slower than the timed
+    # steps: a kind's time per step is its share of the profiled step times the
+    # timed step's own duration.
+    prof_total = sum(v[0] for v in kinds.values())
+    step_ms = total_ms / args.steps
+    scale = step_ms / prof_total
+    # The roofline of the solver: one PCG step (operator + vector kernels, or its
+    # share of the single-launch loop) against the algorithmic bytes of a textbook
+    # PCG step, (8 V + 2 + S) x 4 B per pixel (read p twice, the state X for the
+    # operator's coefficients, delta and r; write delta, r and p; w_SR and the S
+    # pair weights)
+    V = K + 4
+    S_pairs = len(off_s) + len(off_t)
+    pcg_bytes = 4.0 * (8 * V + 2 + S_pairs) * P
+    pcg_ms = sum(kinds[k][0] for k in ("apply", "update", "pcg") if k in kinds) * scale
+    n_pcg = F * N * M
+    pcg_us = 1000.0 * pcg_ms / n_pcg
+    ach = pcg_bytes / (pcg_us * 1e-6) / 1e9
+    traffic = ncu_traffic("pcg_step")
+    alg = algorithmic_bytes(dom, K, P, M, len(off_s), len(off_t), True)
+    design = None
+    if alg and dom in ("apply", "update"):
+        dom_scaled = dom_ms * scale
+        design = {"kernel": kernel_name, "design_bytes_per_launch": alg, "avg_launch_ms": dom_scaled,
+                  "achieved_GBps": alg / (dom_scaled / 1000.0) / 1e9, "frac": alg / (dom_scaled / 1000.0) / 1e9 / peak,
+                  "note": "the kernel's own design bytes (stored coefficient planes) per launch"}
+    roof = {"bound": "hbm", "kernel": "PCG step (" + ("k_pcg_resident" if "pcg" in kinds and tile_rows == -1 else
+                                                      "k_pcg" if "pcg" in kinds else "k_apply + k_update") + ")",
+            "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
+            "peak_source": peak_src, "algorithmic_bytes_per_step": pcg_bytes,
+            "bytes_per_px": 4 * (8 * V + 2 + S_pairs), "pcg_step_us": pcg_us, "pcg_steps_per_video": n_pcg,
+            "frac_survey_bytes": ach / peak, "dominant_kind": dom, "design_roofline": design,
+            "method": "pcg_step_us = (time of the PCG kernels in a profiled step with a CUDA event after every "
+                      "kernel) x (timed step / profiled step) / PCG steps; achieved = algorithmic bytes of one "
+                      f"PCG step / pcg_step_us (profiled step {prof_total:.1f} ms vs timed step {step_ms:.1f} ms)"}
     shares = {k: {"ms_per_step": v[0], "launches": v[1]} for k, v in kinds.items()}
 
     # end to end: the host-buffer entry point, host<->device copies inside the timed region
@@ -406,7 +490,7 @@ def run_gid(args, ws, rank, local):
         preconditioners = []
         sp = gid.Solver(H, W, K, gid.default_weights(off_s))
         sp.set_frame(rgb[0], lab[0])
-        sp.set_apply_tile(tile_rows if tile_rows else 17)   # one operator kernel per PCG step in both arms
+        sp.set_apply_tile(tile_rows if tile_rows and tile_rows > 0 else 17)   # one operator kernel per PCG step in both arms
         for kind in ("jacobi", "block"):
             sp.set_preconditioner(kind)
             for Mi in (10, 15, 20):
@@ -444,7 +528,7 @@ def run_gid(args, ws, rank, local):
 
         sb = gid.Solver(H, W, K, w)
         sb.set_base_colors(b0)
-        sb.set_apply_tile(tile_rows if tile_rows else 17)
+        sb.set_apply_tile(tile_rows if tile_rows and tile_rows > 0 else 17)
         e_ref = video_energies(s, M)
         sb.set_preconditioner("block")
         ratios, Mb = {}, None
@@ -490,13 +574,22 @@ def run_gid(args, ws, rank, local):
     if rank == 0 and not args.no_learned:
         learned = learned_arm(dev, flush)
 
-    cpu = None
+    # the oracle on the host cores (one whole frame), and the per-layer error of the GPU's
+    # solve of that frame (in the timed launch configuration) and of the 64 x 48 workload
+    cpu, parity = None, None
     if rank == 0 and not args.no_cpu:
-        import oracle
-        oracle.build()
-        dt, fps = cpu_sample(0)
-        cpu = {"value": fps, "unit": "frames/s", "cores": 1, "kind": "oracle", "sample": CPU_SAMPLE,
-               "seconds": dt}
+        cpu, Xo, bo, hist = cpu_baseline()
+        s.new_sequence()
+        s.set_frame(rgb[0], lab[0])
+        s.init(0)
+        s.run(N, M)
+        R0, T0 = s.layers()
+        E0, _ = s.energy()
+        parity = {"bar": "every layer <= 1e-3 max-abs, energy <= 1e-4 relative, after the same N x M from the same "
+                         "start",
+                  "video_640x480_K6_frame0": dict(layer_errors(R0.cpu().numpy(), T0.cpu().numpy(), s.base_colors(),
+                                                               E0, Xo, bo, hist[-1].sum()), N=N, M=M, start="cold"),
+                  "single_64x48_K4": parity_64x48()}
 
     if rank == 0:
         out = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": args.steps,
@@ -505,14 +598,42 @@ def run_gid(args, ws, rank, local):
                "config": {"workload": WORKLOAD, "H": H, "W": W, "K": K, "frames_per_step": F, "N_outer": N,
                           "M_inner": M, "l2": "flushed before each step (256 MB write, outside the events)",
                           "parallelism": f"replicas x{ws} (one video per GPU)",
-                          "operator_tile": (f"128x{tile_rows}" if tile_rows else "persistent PCG kernel") +
+                          "operator_tile": pcg_loop_name(s, tile_rows) +
                           (f" (autotuned; us per PCG step {tile_us})" if args.tile is None else " (fixed)")},
                "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
-               "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "final_energy": E,
+               "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "clocks": clk, "final_energy": E,
                "learned_warm_start": learned, "editing": editing, "clustering": clustering,
                "misclustering_correction": correction, "preconditioners": preconditioners,
                "block_jacobi_equal_energy": block_arm}
         print(json.dumps(out), flush=True)
+
+
+def parity_64x48():
+    """The 64 x 48 K = 4 workload (5 x 10, cold start, refinement on) on the GPU
+    and in the oracle: per-layer errors."""
+    import torch
+
+    import oracle as O
+    from paper_1908_01961_b300 import gid
+    cfg = synth.SINGLE_64x48
+    H, W, K = cfg["H"], cfg["W"], cfg["K"]
+    f = synth.SyntheticVideo(H, W, K, cfg["n_cells"], seed=0).frame(0)
+    b0 = synth.initial_base_colors(f.I, f.labels, K).astype(np.float32)
+    off_s, _ = synth.offsets_for(0)
+    s = gid.Solver(H, W, K, gid.default_weights(off_s))
+    s.set_base_colors(b0)
+    s.set_frame(torch.from_numpy(f.I.astype(np.float32)).cuda(), torch.from_numpy(f.labels).cuda())
+    s.init(0)
+    s.run(cfg["N"], cfg["M"])
+    R, T = s.layers()
+    E, _ = s.energy()
+    I = f.I.astype(np.float32).astype(np.float64)
+    C, wsr, om, _ = O.precompute(I, off_s)
+    pb = O.Problem(I, f.labels, b0.astype(np.float64), wsr, om, off_s)
+    Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), cfg["N"], cfg["M"])
+    out = layer_errors(R.cpu().numpy(), T.cpu().numpy(), s.base_colors(), E, Xo, bo, hist[-1].sum())
+    s.close()
+    return dict(out, N=cfg["N"], M=cfg["M"], start="cold")
 
 
 # ---------------------------------------------------------------- learned warm start
@@ -637,8 +758,7 @@ def run_batch(args, ws, rank, local):
             batch.run(N, M)
 
     step()
-    batch.autotune(os.path.join(ROOT, "gpurun_out", "batch_tiles.txt") if os.path.isdir(os.path.join(ROOT, "gpurun_out"))
-                   else None, reps=5)
+    batch.autotune(args.tile_cache, reps=5)
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -758,7 +878,7 @@ def run_stream(args, ws, rank, local):
                "config": {"workload": f"stream_1920x1080_K8: {F} frames, 80 moving Voronoi cells, rotating light; "
                                       "frame 0 cold, then warm starts with temporal pairs", "H": H, "W": W, "K": K,
                           "frames": F, "N_outer": N, "M_inner": M,
-                          "operator_tile": f"128x{tile_rows} (autotuned; us per PCG step {tile_us})",
+                          "operator_tile": pcg_loop_name(s, tile_rows) + f" (autotuned; us per PCG step {tile_us})",
                           "l2": "inputs (20 MB per frame of planes, 190 MB per PCG vector set) exceed the L2"},
                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                               "max": float(lat.max()), "first_frame": float(lat[0])},

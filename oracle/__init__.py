@@ -38,10 +38,11 @@ DEFAULT_WEIGHTS = dict(
 
 
 def build(force: bool = False) -> str:
-    """Compile oracle.c into liboracle.so (gcc, -O2, strict IEEE: no -ffast-math)."""
+    """Compile oracle.c into liboracle.so (gcc, -O2, strict IEEE: no -ffast-math;
+    OpenMP spreads the loops over threads without changing any result)."""
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
-        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
     return _LIB
 
@@ -69,10 +70,21 @@ def lib():
         _lib.or_pcg_variant.restype = ctypes.c_int
         _lib.or_dense_normal.argtypes = [P, D, D, D]
         _lib.or_init_cold.argtypes = [P, D]
+        _lib.or_set_threads.argtypes = [ctypes.c_int]
+        _lib.or_max_threads.restype = ctypes.c_int
         _lib.or_precompute.argtypes = [ctypes.c_int, ctypes.c_int, D, D, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                                        ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_double, ctypes.c_double,
                                        D, D, D, D]
     return _lib
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops (the results do not depend on it)."""
+    lib().or_set_threads(int(n))
+
+
+def max_threads() -> int:
+    return int(lib().or_max_threads())
 
 
 class _Struct(ctypes.Structure):

@@ -6,11 +6,21 @@
  * this file: only the tests, the smoke check and the CPU-baseline leg of the
  * benchmark use it.  It shares no code with the CUDA library.
  *
- * Style: plain, serial, slow, FP64.  Every energy term is written as the list of
+ * Style: plain, slow, FP64.  Every energy term is written as the list of
  * its least-squares residual rows (value f and the sparse Jacobian row a_j), in
  * the order the paper lists the terms.  The Gauss-Newton normal-equation
  * products J^T J p, -J^T F and diag(J^T J) are then the textbook sums over those
  * rows, so a reader can check each term against its equation by eye.
+ *
+ * Order of the FP64 sums (fixed, whatever the thread count, so results are the
+ * same bit for bit on 1 or many threads; OpenMP only spreads the work for the
+ * benchmark's timing): the residual rows are visited in stripes of OR_STRIPE
+ * image rows, all even stripes first, then all odd ones, each stripe in row
+ * order.  A row generated at image row y touches unknowns of rows y - 3 .. y + 3
+ * only (the widest reach is the consistency pairs' radius 3), so two stripes of
+ * one phase never touch the same unknown and may run at once.  Dot products
+ * and per-term energies are summed per fixed chunk (stripe), then over the
+ * chunks in order.
  *
  * Unknowns per pixel (V = K + 4): r_R, r_G, r_B (r = ln R, the log reflectance
  * of eq:clustering-term) and T_0..T_K (eq:imageformation).  Layout [V][H][W].
@@ -36,6 +46,28 @@
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_STRIPE 8   /* image rows per stripe (> 2 x 3, the widest reach of a row) */
+#define OR_CHUNK 4096 /* elements per partial sum of a dot product */
+
+/* Threads used by the parallel loops (timing only; results do not depend on it). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+  omp_set_num_threads(n > 0 ? n : 1);
+#else
+  (void)n;
+#endif
+}
+int or_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
 
 typedef struct {
   int H, W, K;
@@ -109,10 +141,11 @@ static const int DIRS[2][2] = {{0, 1}, {1, 0}}; /* forward differences along x a
  * Enumerate every residual row of the (IRLS-reweighted) decomposition energy
  * eq:giv-energy at state X; the reweighting constants come from state Xw.
  */
-static void or_rows(const or_problem *pb, const double *X, const double *Xw, unsigned mask, or_visit_fn fn, void *ctx) {
-  const int H = pb->H, W = pb->W, K = pb->K;
+static void or_rows_range(const or_problem *pb, const double *X, const double *Xw, unsigned mask, or_visit_fn fn,
+                          void *ctx, int y_begin, int y_end) {
+  const int W = pb->W, K = pb->K;
   or_row row;
-  for (int y = 0; y < H; y++)
+  for (int y = y_begin; y < y_end; y++)
     for (int x = 0; x < W; x++) {
       /* E_data, eq:data-term: sqrt(l_data) (I_c - R_c S_c), R_c = exp(r_c). */
       if (mask & (1u << T_DATA)) {
@@ -234,6 +267,25 @@ static void or_rows(const or_problem *pb, const double *X, const double *Xw, uns
     }
 }
 
+/* Every row in image-row order (visitors whose result depends on the order). */
+static void or_rows(const or_problem *pb, const double *X, const double *Xw, unsigned mask, or_visit_fn fn, void *ctx) {
+  or_rows_range(pb, X, Xw, mask, fn, ctx, 0, pb->H);
+}
+
+/* Every row, in the striped order described at the top of the file; for
+ * visitors that only add into the unknowns the row touches. */
+static void or_rows_striped(const or_problem *pb, const double *X, const double *Xw, unsigned mask, or_visit_fn fn,
+                            void *ctx) {
+  const int ns = (pb->H + OR_STRIPE - 1) / OR_STRIPE;
+  for (int phase = 0; phase < 2; phase++) {
+#pragma omp parallel for schedule(static)
+    for (int st = phase; st < ns; st += 2) {
+      const int y1 = (st + 1) * OR_STRIPE < pb->H ? (st + 1) * OR_STRIPE : pb->H;
+      or_rows_range(pb, X, Xw, mask, fn, ctx, st * OR_STRIPE, y1);
+    }
+  }
+}
+
 /* ---------------- normal-equation products over the rows ---------------- */
 
 typedef struct { const double *p; double *q; } apply_ctx;
@@ -272,19 +324,19 @@ static long nvar(const or_problem *pb) { return (long)(pb->K + 4) * P_of(pb); }
 void or_apply(const or_problem *pb, const double *X, const double *Xw, unsigned mask, const double *p, double *q) {
   memset(q, 0, sizeof(double) * nvar(pb));
   apply_ctx c = {p, q};
-  or_rows(pb, X, Xw, mask, visit_apply, &c);
+  or_rows_striped(pb, X, Xw, mask, visit_apply, &c);
 }
 
 /* g = -J^T F (right-hand side of the normal equations). */
 void or_rhs(const or_problem *pb, const double *X, const double *Xw, unsigned mask, double *g) {
   memset(g, 0, sizeof(double) * nvar(pb));
-  or_rows(pb, X, Xw, mask, visit_rhs, g);
+  or_rows_striped(pb, X, Xw, mask, visit_rhs, g);
 }
 
 /* d = diag(J^T J), the Jacobi preconditioner's inverse. */
 void or_diag(const or_problem *pb, const double *X, const double *Xw, unsigned mask, double *d) {
   memset(d, 0, sizeof(double) * nvar(pb));
-  or_rows(pb, X, Xw, mask, visit_diag, d);
+  or_rows_striped(pb, X, Xw, mask, visit_diag, d);
 }
 
 /* Per-term sum of squared residuals |F_t|^2 (the IRLS surrogate energy). */
@@ -305,10 +357,9 @@ long or_residuals(const or_problem *pb, const double *X, const double *Xw, unsig
 /* E[0..7] = E_data, E_clustering, E_r-sparsity, E_r-consistency, E_monochrome,
  * E_i-sparsity, E_smoothness, E_non-neg, each as its equation defines it
  * (the l1 / l_p / max terms exactly, not their IRLS surrogates). */
-void or_energy(const or_problem *pb, const double *X, double *E) {
-  const int H = pb->H, W = pb->W, K = pb->K;
-  memset(E, 0, sizeof(double) * N_TERMS);
-  for (int y = 0; y < H; y++)
+static void or_energy_range(const or_problem *pb, const double *X, double *E, int y_begin, int y_end) {
+  const int W = pb->W, K = pb->K;
+  for (int y = y_begin; y < y_end; y++)
     for (int x = 0; x < W; x++) {
       long px = (long)y * W + x;
       double S[3], Sbar = 0;
@@ -359,11 +410,35 @@ void or_energy(const or_problem *pb, const double *X, double *E) {
     }
 }
 
+void or_energy(const or_problem *pb, const double *X, double *E) {
+  const int ns = (pb->H + OR_STRIPE - 1) / OR_STRIPE;
+  double *part = calloc((size_t)ns * N_TERMS, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int st = 0; st < ns; st++) {
+    const int y1 = (st + 1) * OR_STRIPE < pb->H ? (st + 1) * OR_STRIPE : pb->H;
+    or_energy_range(pb, X, part + (long)st * N_TERMS, st * OR_STRIPE, y1);
+  }
+  memset(E, 0, sizeof(double) * N_TERMS);
+  for (int st = 0; st < ns; st++)
+    for (int t = 0; t < N_TERMS; t++) E[t] += part[(long)st * N_TERMS + t];
+  free(part);
+}
+
 /* ---------------- Gauss-Newton step with Jacobi-PCG (Sec. 6) ---------------- */
 
 static double dot(const double *a, const double *b, long n) {
+  const long nc = (n + OR_CHUNK - 1) / OR_CHUNK;
+  double *part = malloc(sizeof(double) * (nc > 0 ? nc : 1));
+#pragma omp parallel for schedule(static)
+  for (long c = 0; c < nc; c++) {
+    double s = 0;
+    const long e = (c + 1) * OR_CHUNK < n ? (c + 1) * OR_CHUNK : n;
+    for (long i = c * OR_CHUNK; i < e; i++) s += a[i] * b[i];
+    part[c] = s;
+  }
   double s = 0;
-  for (long i = 0; i < n; i++) s += a[i] * b[i];
+  for (long c = 0; c < nc; c++) s += part[c];
+  free(part);
   return s;
 }
 
@@ -381,6 +456,7 @@ void or_pcg(const or_problem *pb, const double *X, int M, double *delta, double 
   double *p = malloc(sizeof(double) * n), *q = malloc(sizeof(double) * n);
   or_rhs(pb, X, X, ALL_TERMS, g);
   or_diag(pb, X, X, ALL_TERMS, d);
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < n; i++) {
     delta[i] = 0;
     r[i] = g[i];
@@ -393,6 +469,7 @@ void or_pcg(const or_problem *pb, const double *X, int M, double *delta, double 
     or_apply(pb, X, X, ALL_TERMS, p, q);
     double pq = dot(p, q, n);
     double alpha = pq != 0 ? rho / pq : 0.0;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; i++) {
       delta[i] += alpha * p[i];
       r[i] -= alpha * q[i];
@@ -400,6 +477,7 @@ void or_pcg(const or_problem *pb, const double *X, int M, double *delta, double 
     }
     double rho_new = dot(r, z, n);
     double beta = rho != 0 ? rho_new / rho : 0.0;
+#pragma omp parallel for schedule(static)
     for (long i = 0; i < n; i++) p[i] = z[i] + beta * p[i];
     rho = rho_new;
     if (rz) rz[m] = rho;
@@ -439,7 +517,7 @@ void or_block_diag(const or_problem *pb, const double *X, const double *Xw, unsi
   const int V = pb->K + 4;
   memset(B, 0, sizeof(double) * P_of(pb) * V * V);
   block_ctx c = {B, P_of(pb), V};
-  or_rows(pb, X, Xw, mask, visit_block, &c);
+  or_rows_striped(pb, X, Xw, mask, visit_block, &c);
 }
 
 /* Cholesky factor (lower, in place, row-major n x n) of an SPD matrix; returns 0 on a non-positive pivot. */
@@ -580,13 +658,11 @@ int or_pcg_variant(const or_problem *pb, const double *X, int M, int block, int 
  * so the 3K x 3K system is three K x K blocks: A[c][k][l], g[c][k]
  * (A is (3, K, K) row-major, g is (3, K); g = -J^T F).
  */
-void or_dense_normal(const or_problem *pb, const double *X, double *A, double *g) {
-  const int H = pb->H, W = pb->W, K = pb->K;
-  memset(A, 0, sizeof(double) * 3 * K * K);
-  memset(g, 0, sizeof(double) * 3 * K);
+static void or_dense_range(const or_problem *pb, const double *X, double *A, double *g, int y_begin, int y_end) {
+  const int W = pb->W, K = pb->K;
   double sl = sqrt(pb->lambda_data);
   double a[64];
-  for (int y = 0; y < H; y++)
+  for (int y = y_begin; y < y_end; y++)
     for (int x = 0; x < W; x++)
       for (int c = 0; c < 3; c++) {
         double R = exp(X[idx(pb, c, y, x)]);
@@ -599,6 +675,23 @@ void or_dense_normal(const or_problem *pb, const double *X, double *A, double *g
           for (int l = 0; l < K; l++) A[(c * K + k) * K + l] += a[k] * a[l];
         }
       }
+}
+
+void or_dense_normal(const or_problem *pb, const double *X, double *A, double *g) {
+  const int K = pb->K, ns = (pb->H + OR_STRIPE - 1) / OR_STRIPE, na = 3 * K * K + 3 * K;
+  double *part = calloc((size_t)ns * na, sizeof(double));
+#pragma omp parallel for schedule(static)
+  for (int st = 0; st < ns; st++) {
+    const int y1 = (st + 1) * OR_STRIPE < pb->H ? (st + 1) * OR_STRIPE : pb->H;
+    or_dense_range(pb, X, part + (long)st * na, part + (long)st * na + 3 * K * K, st * OR_STRIPE, y1);
+  }
+  memset(A, 0, sizeof(double) * 3 * K * K);
+  memset(g, 0, sizeof(double) * 3 * K);
+  for (int st = 0; st < ns; st++) {
+    for (int i = 0; i < 3 * K * K; i++) A[i] += part[(long)st * na + i];
+    for (int i = 0; i < 3 * K; i++) g[i] += part[(long)st * na + 3 * K * K + i];
+  }
+  free(part);
   /* Intensity regulariser sqrt(l_IR) Delta b_kc and chromaticity regulariser
    * sqrt(l_CR) ((C(b_k) + Delta b_k) - C(b_k))_c: both residuals are zero at
    * Delta b = 0 with unit Jacobian, adding l_IR + l_CR to the diagonal. */
@@ -620,6 +713,7 @@ void or_precompute(int H, int W, const double *I, const double *Iprev, int n_s, 
                    double *omega_t) {
   long P = (long)H * W;
   double *Cp = Iprev ? malloc(sizeof(double) * 3 * P) : NULL;
+#pragma omp parallel for schedule(static)
   for (long i = 0; i < P; i++) {
     double s = I[i] + I[P + i] + I[2 * P + i] + 1e-6;
     for (int c = 0; c < 3; c++) C[c * P + i] = I[c * P + i] / s;
@@ -629,6 +723,7 @@ void or_precompute(int H, int W, const double *I, const double *Iprev, int n_s, 
     }
   }
   static const int N4[4][2] = {{0, 1}, {0, -1}, {1, 0}, {-1, 0}};
+#pragma omp parallel for schedule(static)
   for (int y = 0; y < H; y++)
     for (int x = 0; x < W; x++) {
       long i = (long)y * W + x;
