@@ -522,14 +522,19 @@ int gid_profile_read(gid_ctx* ctx, double* ms, long long* count);
  *   b_dev       out, K x 3 floats, refined colours b_init + Delta b (device) or NULL
  *   errbuf      optional caller buffer of errbuf_len bytes for an error message
  * Returns GID_ERR_INVALID_ARG for a NULL input, K outside 1..GID_MAX_K or a
- * frame beyond 2^28 pixels, GID_ERR_NUMERIC if a block is not positive
- * definite (b_dev then holds b_init), GID_ERR_CUDA on a runtime error.
- * Synchronises the stream before returning.  The first call on each device
- * resolves the array's device address (cudaGetSymbolAddress) with that device
- * current; make that first call before any stream capture.  All calls on a
- * device share the one array and it keeps the last call's contents (the call
- * clears what must start at zero itself): calls that overlap on the GPU, from
- * several streams or threads, race and must be serialised by the caller. */
+ * frame beyond 2^28 pixels, GID_ERR_NUMERIC if a channel's K x K block is not
+ * positive definite (each colour channel is solved on its own: the channels
+ * whose block failed keep b_init in b_dev, the others are refined),
+ * GID_ERR_CUDA on a runtime error.  Copies the small results with ordinary
+ * asynchronous copies and synchronises the stream before returning, so it
+ * cannot be called while the stream is being captured into a CUDA graph.  The
+ * first call on each device resolves the array's device address
+ * (cudaGetSymbolAddress) with that device current and keeps it for the life of
+ * the process: after cudaDeviceReset the call must not be used again in that
+ * process.  All calls on a device share the one array and it keeps the last
+ * call's contents (the call clears what must start at zero itself): calls that
+ * overlap on the GPU, from several streams or threads, race and must be
+ * serialised by the caller. */
 int gid_dense_refine_noalloc(int H, int W, int K, const float* X_dev, const float* rgb_dev,
                              const float* b_init_host, const gid_weights* w, void* stream, double* A_dev,
                              double* g_dev, float* b_dev, char* errbuf, int errbuf_len);

@@ -304,12 +304,11 @@ def recombine(X, b, b_new, gains, mask):
     return R * ratio[m].transpose(2, 0, 1) * S
 
 
-def chromaticity32(I):
-    """C = I / (I_R + I_G + I_B + 1e-6) in float32, in that order of operations
-    (the precision and order the CUDA ingest uses, so that bin and cluster
-    decisions are taken on identical values)."""
-    I = np.asarray(I, np.float32)
-    s = (I[0] + I[1]) + I[2] + np.float32(1e-6)
+def chromaticity(I):
+    """C = I / (I_R + I_G + I_B + 1e-6) in FP64 (Sec. 4.1; the 1e-6 keeps black
+    pixels finite)."""
+    I = np.asarray(I, np.float64)
+    s = (I[0] + I[1]) + I[2] + 1e-6
     return I / s[None]
 
 
@@ -318,7 +317,7 @@ CLUSTER_BINS = 10
 
 def cluster(I, k_max, merge_dist=0.2, max_iter=100):
     """Chromaticity clustering of Sec. 4.1, steps in the paper's order:
-    1. chromaticity C of every pixel;
+    1. chromaticity C of every pixel (FP64);
     2. histogram with 10 partitions per axis of (C_R, C_G, C_B) in [0, 1]
        (values outside, from negative noisy channels, count in the edge bins);
     3. weighted k-means with the bins' mid-points as samples and their
@@ -330,14 +329,14 @@ def cluster(I, k_max, merge_dist=0.2, max_iter=100):
        larger, whose centre becomes the population-weighted mean of both
        (closest pair first; empty clusters are dropped);
     5. every pixel is assigned to its closest centre (its own chromaticity,
-       distances in float64);
+       FP64 distances);
     6. initial base colours: the mean RGB of each cluster's pixels.
     Clusters are ordered by decreasing population (ties by centre order).
     Returns (labels (H, W) uint8, b_init (K', 3) float64, centres (K', 3))."""
     I = np.asarray(I)
-    C = chromaticity32(I)
+    C = chromaticity(I)
     nb = CLUSTER_BINS
-    idx = np.clip((C * np.float32(nb)).astype(np.int32), 0, nb - 1)          # (3, H, W); outside [0, 1] -> edge bins
+    idx = np.clip(np.floor(C * nb).astype(np.int64), 0, nb - 1)              # (3, H, W); outside [0, 1] -> edge bins
     flat = (idx[0] * nb + idx[1]) * nb + idx[2]
     hist = np.bincount(flat.ravel(), minlength=nb ** 3).astype(np.float64)
     mids = (np.stack(np.meshgrid(np.arange(nb), np.arange(nb), np.arange(nb), indexing="ij"), -1).reshape(-1, 3)
@@ -379,8 +378,7 @@ def cluster(I, k_max, merge_dist=0.2, max_iter=100):
         alive.remove(small)
     alive.sort(key=lambda j: (-pw[j], j))
     centres = np.array([cen[j] for j in alive])
-    Cd = C.astype(np.float64)
-    d = ((Cd[None] - centres[:, :, None, None]) ** 2).sum(1)                  # (K', H, W)
+    d = ((C[None] - centres[:, :, None, None]) ** 2).sum(1)                   # (K', H, W)
     labels = d.argmin(axis=0).astype(np.uint8)
     I64 = I.astype(np.float64)
     b = np.array([I64[:, labels == j].mean(axis=1) if np.any(labels == j) else centres[j]

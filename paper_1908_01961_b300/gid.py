@@ -185,8 +185,26 @@ def dense_refine_noalloc(X, rgb, b_init, weights=None, A=None, g=None, b=None, s
     float32 CUDA tensors; A (3, K, K) float64, g (3, K) float64 and b (K, 3)
     float32 are optional caller-allocated CUDA outputs."""
     import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def check(t, name, dtype, shape):
+        if t is None:
+            return
+        if not isinstance(t, torch.Tensor) or t.device != dev or t.dtype != dtype or tuple(t.shape) != shape \
+                or not t.is_contiguous():
+            raise ValueError(f"{name}: need a contiguous {dtype} tensor of shape {shape} on {dev}")
+
+    if not isinstance(X, torch.Tensor) or X.dim() != 3:
+        raise ValueError("X: need a (K+4, H, W) tensor")
     V, H, W = X.shape
     K = V - 4
+    if not 1 <= K <= MAX_K:
+        raise ValueError(f"X has {V} planes: K = {K} is outside 1..{MAX_K}")
+    check(X, "X", torch.float32, (V, H, W))
+    check(rgb, "rgb", torch.float32, (3, H, W))
+    check(A, "A", torch.float64, (3, K, K))
+    check(g, "g", torch.float64, (3, K))
+    check(b, "b", torch.float32, (K, 3))
     bi = np.ascontiguousarray(b_init, dtype=np.float32).reshape(K, 3)
     w = weights if weights is not None else default_weights()
     s = stream.cuda_stream if stream is not None else torch.cuda.current_stream().cuda_stream

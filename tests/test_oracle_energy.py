@@ -279,3 +279,39 @@ def test_cluster_weighted_kmeans_centre_is_population_weighted():
     lab, b, cen = O.cluster(I, 10)
     assert cen.shape == (1, 3)
     assert np.allclose(cen[0], (3 * np.array([0.65, 0.35, 0.05]) + np.array([0.55, 0.45, 0.05])) / 4)
+
+
+def test_cold_start_recovers_direct_shading_when_reflectance_is_the_cluster_colour():
+    """Cold start (the paper states only R's initialisation, from R_cluster, Sec.
+    4.1; T_0 = mean_c I / mean_c R_cluster is this build's reading): on a
+    noise-free frame built by eq:imageformation with R = R_cluster and no
+    indirect light, I_c = R_c T_0, so the cold start must return the true T_0
+    at every pixel and the data residual must vanish."""
+    H, W, K = 9, 13, 3
+    rng = np.random.default_rng(7)
+    labels = rng.integers(0, K, size=(H, W)).astype(np.uint8)
+    b = rng.uniform(0.1, 0.9, size=(K, 3))
+    T0 = rng.uniform(0.2, 1.0, size=(H, W))
+    R = b[labels].transpose(2, 0, 1)
+    I = R * T0[None]
+    pb = make_problem(H, W, K, I=I, labels=labels, b=b)
+    X = pb.init_cold()
+    assert np.abs(X[3] - T0).max() <= 1e-14
+    assert np.all(X[4:] == 0.0)
+    assert np.abs(np.exp(X[:3]) - R).max() <= 1e-15
+    assert pb.energy(X)[0] <= 1e-12
+
+
+def test_cold_start_one_pixel_by_hand():
+    """One pixel with non-grey reflectance and indirect light present:
+    R = (0.2, 0.5, 0.8), T_0 = 0.7, T_1 = 0.3, b_1 = (0.9, 0.1, 0.4), so
+    I = R * (T_0 + b_1 T_1) = (0.194, 0.365, 0.656).  The cold start ignores the
+    indirect light: T_0 = mean_c I / mean_c R = 1.215 / 1.5 = 0.81, T_1 = 0."""
+    b = np.array([[0.2, 0.5, 0.8], [0.9, 0.1, 0.4]])      # colour 1: the reflectance; colour 2: b_1
+    I = np.array([0.194, 0.365, 0.656]).reshape(3, 1, 1)
+    labels = np.zeros((1, 1), np.uint8)
+    pb = make_problem(1, 1, 2, I=I, labels=labels, b=b, off_s=np.zeros((0, 2)), omega=np.zeros((0, 1, 1)))
+    X = pb.init_cold()
+    assert X[3, 0, 0] == pytest.approx(0.81, abs=1e-15)
+    assert np.allclose(np.exp(X[:3, 0, 0]), [0.2, 0.5, 0.8], atol=1e-15)
+    assert X[4, 0, 0] == 0.0 and X[5, 0, 0] == 0.0

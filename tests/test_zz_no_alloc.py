@@ -1,4 +1,4 @@
-"""The allocation-free base-colour step against the context path (GPU).
+"""The allocation-free base-colour step against the context path and the oracle (GPU).
 
 gid_dense_refine_noalloc serves callers that cannot allocate device memory
 themselves -- code inside another framework's memory pool, real-time loops that
@@ -12,6 +12,7 @@ import ctypes
 import numpy as np
 import pytest
 
+import oracle as O
 from harness import Case
 
 pytestmark = pytest.mark.gpu
@@ -53,6 +54,13 @@ def test_noalloc_matches_context_path_twice_in_a_row():
         assert np.abs(A - A_ref).max() <= 1e-5 * np.abs(A_ref).max()
         assert np.abs(g - g_ref).max() <= 1e-4 * np.abs(g_ref).max()
         assert np.abs(b - b_ref).max() <= 1e-5 * max(1.0, np.abs(b_ref).max())
+        # and against the FP64 oracle's normal equations and SVD solve at the same (float32) layers
+        pb = case.oracle_problem()
+        A_o, g_o = pb.dense_normal(X.cpu().numpy().astype(np.float64))
+        b_o = case.b_init + O.dense_solve(A_o, g_o)
+        assert np.abs(A - A_o).max() <= 1e-5 * np.abs(A_o).max()
+        assert np.abs(g - g_o).max() <= 1e-4 * np.abs(g_o).max()
+        assert np.abs(b - b_o).max() <= 1e-4 * max(1.0, np.abs(b_o).max())
 
 
 def test_noalloc_rejects_sizes_beyond_its_limit():
@@ -67,3 +75,26 @@ def test_noalloc_rejects_sizes_beyond_its_limit():
                                       b0.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(w), None,
                                       None, None, None, err, 128)
     assert rc == -1 and b"K must be" in err.value
+
+
+def test_noalloc_binding_checks_its_tensors():
+    """The binding refuses tensors the kernel would index wrongly (dtype, shape,
+    layout, device) before calling into the library."""
+    from paper_1908_01961_b300 import gid
+    case = Case(H=16, W=24, K=3, n_cells=5, seed=4)
+    X = state(case, 3)
+    rgb, _ = case.gpu_inputs()
+    ok = dict(A=torch.zeros((3, 3, 3), dtype=torch.float64, device="cuda"),
+              g=torch.zeros((3, 3), dtype=torch.float64, device="cuda"),
+              b=torch.zeros((3, 3), dtype=torch.float32, device="cuda"))
+    bad = [dict(X=X.double()), dict(X=X.transpose(1, 2).contiguous().transpose(1, 2)), dict(X=X.cpu()),
+           dict(rgb=rgb[:, :8]), dict(A=ok["A"].float()), dict(g=torch.zeros((3, 2), dtype=torch.float64,
+                                                                              device="cuda")),
+           dict(b=torch.zeros((2, 3), dtype=torch.float32, device="cuda"))]
+    for change in bad:
+        args = dict(X=X, rgb=rgb, **ok)
+        args.update(change)
+        with pytest.raises(ValueError):
+            gid.dense_refine_noalloc(args["X"], args["rgb"], case.b_init, gid.default_weights(), args["A"],
+                                     args["g"], args["b"])
+    gid.dense_refine_noalloc(X, rgb, case.b_init, gid.default_weights(), **ok)
