@@ -19,6 +19,8 @@ Command line:
     python -m paper_1908_01961_b300.warmstart train --frames 1000 --steps 6000 --out FILE.npy
     python -m paper_1908_01961_b300.warmstart evaluate --weights FILE.npy --eval-frames 20
     python -m paper_1908_01961_b300.warmstart sensitivity --eval-frames 4
+    python -m paper_1908_01961_b300.warmstart finetune-energy --weights FILE.npy --frames 500 --steps 2000 \
+        --lr 2e-4 --out FILE2.npy --eval-frames 50
 """
 from __future__ import annotations
 
@@ -47,7 +49,8 @@ LOSS_WEIGHTS = (1.0, 1.0, 10.0)
 # weight 0 for T > 0); above ~0.01 the start's indirect layers are mostly zero.
 ZERO_BELOW = 0.01
 HERE = os.path.dirname(os.path.abspath(__file__))
-DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart_K6.npy")
+# the network trained on the plain solver's layers, then fine-tuned on the energy (train_energy)
+DEFAULT_WEIGHTS = os.path.join(HERE, "weights", "warmstart_K6_energy.npy")
 
 
 def solver_weights():
@@ -140,6 +143,50 @@ def train(net, data, steps, batch=8, size=256, lr=2e-3, lr_min=2e-5, seed=0, log
     return hist
 
 
+def train_energy(net, data, steps, batch=8, size=256, lr=2e-4, lr_min=2e-6, seed=0, m_inner=M_INNER, log=None,
+                 log_every=250):
+    """Fine-tuning on the decomposition energy (eq:giv-energy) itself: each step
+    the network predicts the layers of a batch of crops, the solver takes one
+    Gauss-Newton step of the energy from every prediction (the crop as a frame
+    of its own: its pixels, labels and palette), and the network regresses onto
+    the improved layers.  The gradient of the squared distance to them is, at
+    the prediction, the Gauss-Newton descent direction of the energy, so the
+    network is pulled toward states the solver would move to next, not toward
+    a fixed plain-solver result.  Adam with a cosine learning-rate decay;
+    returns the logged (step, loss, mean energy of the predictions) triples."""
+    import torch
+    gen = torch.Generator().manual_seed(seed)
+    s = gid.Solver(size, size, K, solver_weights())
+    hist = []
+    t0 = time.time()
+    for step in range(steps):
+        a = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(1, steps - 1)))
+        rgb, lab, pal, _, _ = data.crops(gen, batch, size)
+        rp, Tp = net.forward(rgb, lab, pal)
+        rt, Tt = torch.empty_like(rp), torch.empty_like(Tp)
+        pal_h = pal.cpu().numpy()
+        want = step % log_every == 0 or step == steps - 1
+        e_sum = 0.0
+        for i in range(batch):
+            s.set_base_colors(pal_h[i])
+            s.set_frame(rgb[i], lab[i])
+            s.set_state(torch.cat([rp[i], Tp[i]]).contiguous())
+            if want:
+                e_sum += s.energy()[0]
+            s.run(1, m_inner)
+            X = s.state()
+            rt[i].copy_(X[:3])
+            Tt[i].copy_(X[3:])
+        loss = net.train_step(rgb, lab, pal, rt, Tt, a, sync_loss=want)
+        if want:
+            hist.append((step, loss, e_sum / batch))
+            if log:
+                log(f"energy step {step} lr {a:.2e} loss {loss:.3e} mean crop energy {e_sum / batch:.4e} "
+                    f"({time.time() - t0:.1f} s)")
+    s.close()
+    return hist
+
+
 def energies(solver, n_outer=N_OUTER, m_inner=M_INNER):
     """Exact energy (total, and per term: rows of 8) after each of n_outer single
     Gauss-Newton steps; row 0 is the starting state."""
@@ -186,13 +233,17 @@ def evaluate(net, frames, n_outer=N_OUTER, m_inner=M_INNER, zero_below=(None,), 
     return out
 
 
-def sensitivity(frames, amplitudes=(0.001, 0.003, 0.01), seed=0, n_outer=N_OUTER, m_inner=M_INNER, log=None):
+def sensitivity(frames, amplitudes=(0.001, 0.003, 0.01), blurs=(1.0, 2.0), seed=0, n_outer=N_OUTER,
+                m_inner=M_INNER, log=None):
     """How accurate a start must be to save Gauss-Newton steps: per frame, the
     plain solve's result X* (cold start, n_outer steps) plus Gaussian noise of
-    each amplitude (indirect values then clipped at 0), one base-colour step,
-    then the steps needed to return to the plain solve's final energy
-    (n_outer + 1 if not within n_outer)."""
+    each amplitude (indirect values then clipped at 0), and X* blurred by a
+    Gaussian of each width in pixels (the best a predictor of the solution's
+    smooth part alone could do), each followed by one base-colour step, then
+    the steps needed to return to the plain solve's final energy (n_outer + 1
+    if not within n_outer)."""
     import torch
+    from scipy.ndimage import gaussian_filter
     rng = np.random.default_rng(seed)
     s = gid.Solver(H, W, K, solver_weights())
     out = []
@@ -205,18 +256,19 @@ def sensitivity(frames, amplitudes=(0.001, 0.003, 0.01), seed=0, n_outer=N_OUTER
         E_star, _ = s.energy()
         Xs = s.state().cpu().numpy()
         rec = dict(E_star=E_star, steps={})
-        for a in (0.0,) + tuple(amplitudes):
-            X0 = Xs + rng.normal(0.0, a, Xs.shape) if a else Xs.copy()
+        starts = [(str(a), Xs + rng.normal(0.0, a, Xs.shape) if a else Xs.copy()) for a in (0.0,) + tuple(amplitudes)]
+        starts += [(f"blur{sg}", np.stack([gaussian_filter(p, sg) for p in Xs])) for sg in blurs]
+        for key, X0 in starts:
             X0[4:] = np.maximum(X0[4:], 0.0)
             s.set_base_colors(b)
             s.set_state(torch.from_numpy(np.ascontiguousarray(X0, np.float32)).cuda())
             s.base_color_step()
             E, _ = energies(s, n_outer, m_inner)
             hit = np.nonzero(E <= E_star)[0]
-            rec["steps"][str(a)] = int(hit[0]) if len(hit) else n_outer + 1
+            rec["steps"][key] = int(hit[0]) if len(hit) else n_outer + 1
         out.append(rec)
         if log:
-            log(f"frame {i}: steps back to the plain solve's energy by start noise RMS: {rec['steps']}")
+            log(f"frame {i}: steps back to the plain solve's energy by start noise RMS / blur width: {rec['steps']}")
     s.close()
     return out
 
@@ -229,7 +281,7 @@ def load_net(path=DEFAULT_WEIGHTS, stream=None):
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
-    ap.add_argument("cmd", choices=("train", "evaluate", "sensitivity"))
+    ap.add_argument("cmd", choices=("train", "finetune-energy", "evaluate", "sensitivity"))
     ap.add_argument("--frames", type=int, default=1000)
     ap.add_argument("--steps", type=int, default=6000)
     ap.add_argument("--batch", type=int, default=8)
@@ -271,6 +323,19 @@ def main(argv=None):
         report.update(train_frames=a.frames, steps=a.steps, batch=a.batch, crop=256, lr=a.lr,
                       loss_weights=list(a.loss_weights),
                       train_seconds=time.time() - t2, loss=hist)
+        os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
+        np.save(a.out, net.weights())
+        log(f"saved {a.out}")
+        del data
+    elif a.cmd == "finetune-energy":
+        net = load_net(a.weights)
+        frames = generate(range(TRAIN_SEED0, TRAIN_SEED0 + a.frames))
+        data = Dataset(frames, log=log)
+        del frames
+        t2 = time.time()
+        hist = train_energy(net, data, a.steps, a.batch, lr=a.lr, seed=a.seed, log=log)
+        report.update(start_weights=os.path.basename(a.weights), train_frames=a.frames, steps=a.steps,
+                      batch=a.batch, crop=256, lr=a.lr, train_seconds=time.time() - t2, loss=hist)
         os.makedirs(os.path.dirname(os.path.abspath(a.out)), exist_ok=True)
         np.save(a.out, net.weights())
         log(f"saved {a.out}")
