@@ -271,6 +271,21 @@ def run_reference(args, ws, rank):
     print(json.dumps(out), flush=True)
 
 
+def sub_bench(*argv):
+    """Another workload of this file in a child process (its own CUDA context);
+    the child's JSON line, reduced to the figures the main line reports."""
+    try:
+        p = subprocess.run([sys.executable, os.path.abspath(__file__), *argv], capture_output=True, text=True,
+                           timeout=1200, env=dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0"))
+        line = [l for l in p.stdout.strip().splitlines() if l.startswith("{")][-1]
+        d = json.loads(line)
+    except Exception as e:  # reported, never fatal for the main measurement
+        return {"error": f"{type(e).__name__}: {e}"[:300]}
+    keep = ("metric", "value", "unit", "ms_per_step", "pixels_per_s", "latency_ms", "frames_per_s", "gpu_launches",
+            "clocks", "config")
+    return {k: d[k] for k in keep if k in d}
+
+
 def pcg_loop_name(s, rows):
     if rows == -1:
         _, (tw, th, nb) = s.pcg_layout()
@@ -591,6 +606,13 @@ def run_gid(args, ws, rank, local):
     if rank == 0 and not args.no_learned:
         learned = learned_arm(dev, flush)
 
+    # the batch of 24 uneven videos and the 1080p stream, each in a process of its own
+    batch_line, stream_line = None, None
+    if rank == 0 and not args.no_extras:
+        torch.cuda.synchronize()
+        batch_line = sub_bench("--workload", "batch", "--steps", "1", "--warmup", "2")
+        stream_line = sub_bench("--workload", "stream", "--warmup", "1")
+
     # the oracle on the host cores (one whole frame), and the per-layer error of the GPU's
     # solve of that frame (in the timed launch configuration) and of the 64 x 48 workload
     cpu, parity = None, None
@@ -621,6 +643,7 @@ def run_gid(args, ws, rank, local):
                "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "clocks": clk, "final_energy": E,
                "learned_warm_start": learned, "editing": editing, "clustering": clustering,
                "misclustering_correction": correction, "preconditioners": preconditioners,
+               "batch_24_videos": batch_line, "stream_1080p": stream_line,
                "block_jacobi_equal_energy": block_arm}
         print(json.dumps(out), flush=True)
 

@@ -328,11 +328,12 @@ int gid_get_preconditioner(const gid_ctx* ctx);
  * and state (CUDA events on the context stream) and keep the fastest.  Writes
  * the chosen rows (0 = persistent, GID_PCG_RESIDENT) to *rows_out and the six
  * timings (us per PCG step; shapes 2, 4, 8, 17, persistent, resident, -1 if
- * unavailable) to us_out[6]; either may be NULL.  The single-launch loops are
+ * unavailable) to us_out[GID_AUTOTUNE_TIMINGS]; either may be NULL.  The single-launch loops are
  * timed as the difference of two Gauss-Newton steps (reps + 2 and 2 PCG
  * steps), so that the linearisation does not count.  Needs gid_set_frame and a state; leaves the state X
  * unchanged (the PCG vectors are scratch until the next gid_run).  Call it
  * between runs.  Synchronises. */
+#define GID_AUTOTUNE_TIMINGS 6
 int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
 
 /* ---- batches of videos (many videos of uneven size, one graph per step) ---- */
@@ -366,8 +367,10 @@ int gid_batch_run(gid_batch* batch, int n_outer, int m_inner);
 
 /* Choose every video's operator tile shape: from the cache file (lines
  * "H W K rows") if it lists the video's shape, else by gid_autotune(reps) on
- * the video's current frame and state, then append the new shapes to the file
- * (cache_path may be NULL: no cache).  Needs frames and states.  Synchronises. */
+ * the video's current frame and state (the fastest multi-kernel tile shape:
+ * batches do not run the single-launch loops), then append the new shapes to
+ * the file (cache_path may be NULL: no cache).  Needs frames and states.
+ * Synchronises. */
 int gid_batch_autotune(gid_batch* batch, const char* cache_path, int reps);
 
 /* ---- learned initial state (BF16 encoder-decoder) ---- */

@@ -1723,13 +1723,17 @@ extern "C" int gid_batch_autotune(gid_batch* b, const char* cache_path, int reps
   bool dirty = false;
   for (int i = 0; i < b->n; i++) {
     gid_ctx* c = b->ctx[i];
-    int rows = -1;
+    int rows = 0;
+    bool found = false;
     for (auto& r : cache)
-      if (r[0] == c->H && r[1] == c->W && r[2] == c->K) rows = r[3];
-    if (rows < 0) {
-      float us[5];
+      if (r[0] == c->H && r[1] == c->W && r[2] == c->K) {
+        rows = r[3];
+        found = true;
+      }
+    if (!found) {
+      float us[GID_AUTOTUNE_TIMINGS];
       if (int rc = gid_autotune(c, reps, &rows, us)) return bfail(b, rc, gid_last_error(c));
-      if (rows == 0) {  // batches run the multi-kernel PCG: keep its fastest tile shape
+      if (rows <= 0) {  // batches run the multi-kernel PCG: keep its fastest tile shape
         const int cand[4] = {2, 4, 8, 17};
         int jb = 0;
         for (int j = 1; j < 4; j++)
@@ -1739,6 +1743,7 @@ extern "C" int gid_batch_autotune(gid_batch* b, const char* cache_path, int reps
       cache.push_back({c->H, c->W, c->K, rows});
       dirty = true;
     }
+    if (rows <= 0) rows = 17;  // a cache line naming a single-launch loop: batches run the multi-kernel PCG
     if (int rc = gid_set_apply_tile(c, rows)) return bfail(b, rc, gid_last_error(c));
   }
   if (dirty && cache_path) {

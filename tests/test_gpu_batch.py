@@ -1,10 +1,12 @@
 """Batches of videos of uneven size (one CUDA graph launch per frame-step)
-against the same videos solved one context at a time (GPU)."""
+against the same videos solved one context at a time, and against the FP64
+oracle (GPU)."""
 import os
 
 import numpy as np
 import pytest
 
+import oracle as O
 from harness import Case
 
 pytestmark = pytest.mark.gpu
@@ -75,3 +77,45 @@ def test_batch_autotune_cache(tmp_path):
         E, _ = v.energy()
         assert np.isfinite(E)
     assert os.path.getsize(path) > 0
+
+
+def test_batch_matches_oracle():
+    """Every video of an uneven batch (autotuned loops) against the oracle:
+    frame 0 from the cold start, frame 1 warm with temporal pairs, the oracle
+    starting frame 1 from the GPU's own frame-0 state (3 x 6 each); every layer
+    within 1e-3 max-abs and the energy within 1e-4 relative."""
+    from paper_1908_01961_b300 import gid
+    cs = cases()
+    weights = [gid.default_weights(c.off_s, c.off_t if c.temporal else None, temporal=int(c.temporal)) for c in cs]
+    b = gid.Batch([(c.H, c.W, c.K) for c in cs], weights)
+    for v, c in zip(b.videos, cs):
+        v.set_base_colors(c.b_init)
+    ins = [c.gpu_inputs(0) for c in cs]
+    b.set_frames([i[0] for i in ins], [i[1] for i in ins])
+    b.init(0)
+    b.autotune(None, reps=2)
+    b.init(0)
+    b.run(3, 6)
+    prev = []
+    for v, c in zip(b.videos, cs):
+        R, T = v.layers()
+        E, _ = v.energy()
+        pb = c.oracle_problem(0)
+        Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), 3, 6)
+        assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
+        assert np.abs(v.base_colors() - bo).max() <= 1e-3
+        assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+        prev.append((v.state().cpu().numpy().astype(np.float64), v.base_colors().astype(np.float64)))
+    ins = [c.gpu_inputs(1) for c in cs]
+    b.set_frames([i[0] for i in ins], [i[1] for i in ins])
+    b.init(1)
+    b.run(3, 6)
+    for v, c, (Xp, bp) in zip(b.videos, cs, prev):
+        R, T = v.layers()
+        E, _ = v.energy()
+        pb = c.oracle_problem(1, rprev=Xp[:3], b=bp) if c.temporal else c.oracle_problem(1, b=bp)
+        Xo, bo, hist = O.solve_frame(pb, Xp, 3, 6)
+        assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
+        assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
