@@ -359,17 +359,33 @@ int gid_batch_set_frames(gid_batch* batch, const float* const* rgb_dev, const ui
 int gid_batch_init(gid_batch* batch, int mode);
 int gid_batch_new_sequence(gid_batch* batch);
 
-/* gid_run(n_outer, m_inner) for every video as ONE CUDA graph launch: each
- * video's launch sequence is a branch of the graph (recorded once per
- * configuration), so the videos' kernels run concurrently.  Batches always use
- * the multi-kernel PCG (tile rows 2, 4, 8 or 17).  Asynchronous. */
+/* gid_run(n_outer, m_inner) for every video as ONE CUDA graph launch
+ * (recorded once per configuration).  Work-list form (the default, when every
+ * video uses the Jacobi preconditioner): per Gauss-Newton step each video
+ * linearises on its own stream, then each of the M PCG steps (Sec. 6.1) is one
+ * operator launch and one vector launch per distinct K covering the tiles and
+ * planes of every video with that K (operator tiles of 128 x 17 pixels), then
+ * each video takes its base-colour step on its own stream.  Branch form
+ * (gid_batch_set_worklist(batch, 0), or any video with the block
+ * preconditioner): each video's own multi-kernel launch sequence (tile rows
+ * 2, 4, 8 or 17, as gid_set_apply_tile / gid_batch_autotune chose) is a branch
+ * of the graph.  Per video the two forms compute the same arithmetic except
+ * for the grouping of FP32 partial sums in the PCG reductions (tile shape and
+ * vector-block count), so their results agree to rounding, not bit for bit.
+ * Asynchronous. */
 int gid_batch_run(gid_batch* batch, int n_outer, int m_inner);
 
-/* Choose every video's operator tile shape: from the cache file (lines
- * "H W K rows") if it lists the video's shape, else by gid_autotune(reps) on
- * the video's current frame and state (the fastest multi-kernel tile shape:
- * batches do not run the single-launch loops), then append the new shapes to
- * the file (cache_path may be NULL: no cache).  Needs frames and states.
+/* on != 0: the work-list form of gid_batch_run (default); 0: the branch form.
+ * Takes effect at the next gid_batch_run (graphs of both forms are kept).
+ * GID_ERR_INVALID_ARG for a NULL batch. */
+int gid_batch_set_worklist(gid_batch* batch, int on);
+
+/* Choose every video's operator tile shape for the branch form: from the
+ * cache file (lines "H W K rows") if it lists the video's shape, else by
+ * gid_autotune(reps) on the video's current frame and state (the fastest
+ * multi-kernel tile shape: batches do not run the single-launch loops), then
+ * append the new shapes to the file (cache_path may be NULL: no cache).  The
+ * work-list form always uses 17-row tiles.  Needs frames and states.
  * Synchronises. */
 int gid_batch_autotune(gid_batch* batch, const char* cache_path, int reps);
 

@@ -312,6 +312,8 @@ struct Launch {
     cudaFuncSetAttribute(k_apply<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 4>));
     cudaFuncSetAttribute(k_apply<K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 8>));
     cudaFuncSetAttribute(k_apply<K, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 17>));
+    cudaFuncSetAttribute(k_apply_multi<K, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)sizeof(ApplyTile<K, 17>));
   }
   static void apply(const gid_ctx* c, int mode, int first, int it, const float* pin, float* pout, float* qout) {
     switch (c->apply_th) {
@@ -415,6 +417,14 @@ struct Launch {
     c->res_threads = threads;
     c->res_smem = smem;
     c->res_blocks = nb;
+  }
+  // Work-list PCG steps of a batch's videos with this K (operator tiles of 128 x 17).
+  static void apply_multi(cudaStream_t s, const MultiVideo* vids, int nv, const CUtensorMap* maps, int first, int it,
+                          int blocks) {
+    k_apply_multi<K, 17><<<blocks, dim3(BX, 17), sizeof(ApplyTile<K, 17>), s>>>(vids, nv, maps, first, it);
+  }
+  static void update_multi(cudaStream_t s, const MultiVideo* vids, int nv, int it, int last, int blocks) {
+    k_update_multi<K><<<blocks, 256, 0, s>>>(vids, nv, it, last);
   }
   // Resident blocks of the base-colour step on this device (SMs x blocks per SM).
   static int dense_capacity(const gid_ctx*) {
@@ -1523,8 +1533,10 @@ struct gid_batch {
     std::string key;
     cudaGraphExec_t exec;
     long long kernels;
+    std::vector<void*> tables;  // device work-list tables the graph's launches read
   };
   std::vector<Graph> graphs;
+  bool worklist = true;  // PCG steps as work-list launches per K (gid_batch_set_worklist)
   std::string err;
 };
 
@@ -1551,7 +1563,11 @@ extern "C" void gid_batch_destroy(gid_batch* b) {
     cudaStreamSynchronize(c->stream);
     gid_destroy(c);
   }
-  for (auto& g : b->graphs) cudaGraphExecDestroy(g.exec);
+  if (b->bs) cudaStreamSynchronize(b->bs);
+  for (auto& g : b->graphs) {
+    cudaGraphExecDestroy(g.exec);
+    for (void* p : g.tables) cudaFree(p);
+  }
   for (auto s : b->streams) cudaStreamDestroy(s);
   for (auto e : b->ev_join) cudaEventDestroy(e);
   if (b->bs) cudaStreamDestroy(b->bs);
@@ -1640,11 +1656,163 @@ extern "C" int gid_batch_new_sequence(gid_batch* b) {
 // One graph per batch configuration: every video's run is a branch forked from
 // and joined to the batch stream, so the whole frame-step of all videos is one
 // graph launch and the videos' kernels run concurrently.
+// The work-list form of a batch's run, enqueued for capture on b->bs: per
+// The videos of a batch that share K, with their work-list tables.
+struct WorkGroup {
+  int K;
+  std::vector<int> vid;
+  MultiVideo* dv = nullptr;
+  CUtensorMap* dm = nullptr;
+  int tiles = 0, upd = 0;
+};
+
+// The device tables of the work-list launches (made before the capture: the
+// allocation and the copies are not capturable).  False on a CUDA error.
+static bool build_worklist(gid_batch* b, std::vector<WorkGroup>& groups, std::vector<void*>& tables) {
+  constexpr int TH = 17;
+  using Group = WorkGroup;
+  for (int i = 0; i < b->n; i++) {
+    Group* gp = nullptr;
+    for (auto& gr : groups)
+      if (gr.K == b->ctx[i]->K) gp = &gr;
+    if (!gp) {
+      groups.push_back(Group{b->ctx[i]->K, {}});
+      gp = &groups.back();
+    }
+    gp->vid.push_back(i);
+  }
+  for (auto& gr : groups) {
+    const int nv = (int)gr.vid.size();
+    std::vector<MultiVideo> hv(nv);
+    std::vector<CUtensorMap> hm(2 * nv);
+    long total_items = 0;
+    for (int v = 0; v < nv; v++) total_items += (long)b->ctx[gr.vid[v]]->V * (b->ctx[gr.vid[v]]->plane / 4);
+    const int wave = b->ctx[gr.vid[0]]->upd_cap;
+    for (int v = 0; v < nv; v++) {
+      gid_ctx* c = b->ctx[gr.vid[v]];
+      const gid_ctx::Maps* m = tile_maps(c, c->z, TH);
+      if (!m) return false;
+      hm[2 * v] = m->r;
+      hm[2 * v + 1] = m->t;
+      MultiVideo& mv = hv[v];
+      memset(&mv, 0, sizeof(mv));
+      mv.P = params(c);
+      mv.p = c->pA;
+      mv.ntx = (c->W + VTW - 1) / VTW;
+      mv.ntiles = mv.ntx * ((c->H + TH - 1) / TH);
+      const long items = (long)c->V * (c->plane / 4);
+      mv.nupd = (int)std::max(1L, std::min({(long)std::lround((double)wave * items / total_items), (items + 255) / 256,
+                                            (long)c->nbmax}));
+      mv.tile0 = gr.tiles;
+      mv.upd0 = gr.upd;
+      gr.tiles += mv.ntiles;
+      gr.upd += mv.nupd;
+    }
+    if (cudaMalloc(&gr.dv, sizeof(MultiVideo) * nv) != cudaSuccess) return false;
+    tables.push_back(gr.dv);
+    if (cudaMalloc(&gr.dm, sizeof(CUtensorMap) * 2 * nv) != cudaSuccess) return false;
+    tables.push_back(gr.dm);
+    if (cudaMemcpy(gr.dv, hv.data(), sizeof(MultiVideo) * nv, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(gr.dm, hm.data(), sizeof(CUtensorMap) * 2 * nv, cudaMemcpyHostToDevice) != cudaSuccess)
+      return false;
+  }
+  return true;
+}
+
+static void enqueue_apply_multi(gid_batch* b, const WorkGroup& gr, int m) {
+  const int nv = (int)gr.vid.size(), first = m == 1 ? 1 : 0;
+  switch (gr.K) {
+    case 1: Launch<1>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 2: Launch<2>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 3: Launch<3>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 4: Launch<4>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 5: Launch<5>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 6: Launch<6>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 7: Launch<7>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 8: Launch<8>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    case 9: Launch<9>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+    default: Launch<10>::apply_multi(b->bs, gr.dv, nv, gr.dm, first, m, gr.tiles); break;
+  }
+}
+
+static void enqueue_update_multi(gid_batch* b, const WorkGroup& gr, int m, int last) {
+  switch (gr.K) {
+    case 1: Launch<1>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 2: Launch<2>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 3: Launch<3>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 4: Launch<4>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 5: Launch<5>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 6: Launch<6>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 7: Launch<7>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 8: Launch<8>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    case 9: Launch<9>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+    default: Launch<10>::update_multi(b->bs, gr.dv, (int)gr.vid.size(), m, last, gr.upd); break;
+  }
+}
+
+// Per Gauss-Newton step every video's linearisation on its own stream, then M
+// PCG steps as one operator launch and one vector launch per K over all videos
+// with that K (k_apply_multi / k_update_multi, operator tiles of 128 x 17,
+// about one wave of vector blocks per launch split by plane size), then every
+// video's base-colour step on its own stream.  Returns the kernels enqueued,
+// < 0 on error.
+static long long enqueue_worklist(gid_batch* b, std::vector<WorkGroup>& groups, int n_outer, int m_inner,
+                                  const std::vector<int>& refine) {
+  long long kernels = 0;
+  auto fork_join = [&](auto enqueue_one) -> bool {
+    if (cudaEventRecord(b->ev_in, b->bs) != cudaSuccess) return false;
+    for (int i = 0; i < b->n; i++) {
+      gid_ctx* c = b->ctx[i];
+      if (cudaStreamWaitEvent(b->streams[i], b->ev_in, 0) != cudaSuccess) return false;
+      kernels += enqueue_one(c, i);
+      if (cudaEventRecord(b->ev_join[i], b->streams[i]) != cudaSuccess ||
+          cudaStreamWaitEvent(b->bs, b->ev_join[i], 0) != cudaSuccess)
+        return false;
+    }
+    return true;
+  };
+  for (int n = 0; n < n_outer; n++) {
+    bool ok = fork_join([&](gid_ctx* c, int) -> long long {
+      c->last_m_inner = m_inner;
+      c->hist_valid = false;
+      GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr);
+      return 1;
+    });
+    if (!ok) return -1;
+    for (int m = 1; m <= m_inner; m++) {
+      for (auto& gr : groups) {
+        enqueue_apply_multi(b, gr, m);
+        kernels++;
+      }
+      for (auto& gr : groups) {
+        enqueue_update_multi(b, gr, m, m == m_inner ? 1 : 0);
+        kernels++;
+      }
+    }
+    ok = fork_join([&](gid_ctx* c, int i) -> long long {
+      if (!refine[i]) return 0;
+      GID_DISPATCH(c, dense, c, 1);
+      return 1;
+    });
+    if (!ok) return -1;
+  }
+  return cudaGetLastError() == cudaSuccess ? kernels : -1;
+}
+
+extern "C" int gid_batch_set_worklist(gid_batch* b, int on) {
+  if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
+  b->worklist = on != 0;
+  return GID_OK;
+}
+
 extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
   gid::NvtxRange nvtx_range("gid_batch_run");
   if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
   if (n_outer < 1 || m_inner < 1) return bfail(b, GID_ERR_INVALID_ARG, "n_outer >= 1 and m_inner >= 1");
-  std::string key = std::to_string(n_outer) + "," + std::to_string(m_inner);
+  // the work-list form needs Jacobi PCG in every video
+  bool wl = b->worklist;
+  for (int i = 0; i < b->n; i++) wl = wl && b->ctx[i]->precond == GID_PRECOND_JACOBI;
+  std::string key = std::to_string(n_outer) + "," + std::to_string(m_inner) + (wl ? ",w" : ",b");
   std::vector<int> refine(b->n);
   for (int i = 0; i < b->n; i++) {
     gid_ctx* c = b->ctx[i];
@@ -1658,10 +1826,21 @@ extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
     if (e.key == key) g = &e;
   if (!g) {
     long long kernels = 0;
+    std::vector<void*> tables;
+    std::vector<WorkGroup> groups;
+    if (wl && !build_worklist(b, groups, tables)) {
+      cudaGetLastError();
+      for (void* p : tables) cudaFree(p);
+      return bfail(b, GID_ERR_CUDA, "batch work-list tables");
+    }
     GID_BTRY(b, cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
     int rc = GID_OK;
     if (cudaEventRecord(b->ev_in, b->bs) != cudaSuccess) rc = GID_ERR_CUDA;
-    for (int i = 0; i < b->n && !rc; i++) {
+    if (wl && !rc) {
+      kernels = enqueue_worklist(b, groups, n_outer, m_inner, refine);
+      if (kernels < 0) rc = GID_ERR_CUDA;
+    }
+    for (int i = 0; i < b->n && !rc && !wl; i++) {
       gid_ctx* c = b->ctx[i];
       if (cudaStreamWaitEvent(b->streams[i], b->ev_in, 0) != cudaSuccess) {
         rc = GID_ERR_CUDA;
@@ -1679,13 +1858,17 @@ extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
     cudaError_t e = cudaStreamEndCapture(b->bs, &graph);
     if (rc || e != cudaSuccess) {
       if (graph) cudaGraphDestroy(graph);
+      for (void* p : tables) cudaFree(p);
       return bfail(b, rc ? rc : GID_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e));
     }
     cudaGraphExec_t exec = nullptr;
     e = cudaGraphInstantiate(&exec, graph, 0);
     cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return bfail(b, GID_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
-    b->graphs.push_back({key, exec, kernels});
+    if (e != cudaSuccess) {
+      for (void* p : tables) cudaFree(p);
+      return bfail(b, GID_ERR_CUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+    }
+    b->graphs.push_back({key, exec, kernels, tables});
     g = &b->graphs.back();
   }
   // replay after everything already queued for the videos and the caller

@@ -1184,6 +1184,92 @@ __global__ void __launch_bounds__(256, 2) k_update(Params P, int it, int nb_prev
   if (threadIdx.x == 0) pcg_partials(P, PART_RZ, it)[blockIdx.x] = bs;
 }
 
+// ---------------------------------------------------------------- work-list PCG steps of a batch
+
+// One video of a work-list launch: the PCG steps of every video of a batch
+// that shares K run as one operator launch over all their tiles and one vector
+// launch over all their planes, so that small videos do not pay a launch and a
+// barely filled wave each, and large ones no wave tail.  Each video keeps its
+// own scalars and block partials (its own Params); a block finds its video
+// from its index.  Device memory, written by the host when the batch's graph
+// is captured.
+struct MultiVideo {
+  Params P;
+  const float* p;  // the video's PCG direction p (updated in place)
+  int ntx;         // operator tiles per row
+  int ntiles;      // operator tiles
+  int nupd;        // vector-step blocks
+  int tile0, upd0; // the video's first block in the operator / vector launch
+};
+
+// The video (index into vids) that owns block b of a launch, by first[v] =
+// tile0 or upd0, copied into shared memory; returns the block's index within
+// its video.  All threads call.
+template <bool UPD>
+__device__ __forceinline__ int multi_video(const MultiVideo* __restrict__ vids, int nv, MultiVideo& mv, int& v) {
+  __shared__ int vsel;
+  const int tid = tid_flat(), nth = blockDim.x * blockDim.y, b = blockIdx.x;
+  if (tid == 0) {
+    int s = 0;
+    while (s + 1 < nv && (UPD ? vids[s + 1].upd0 : vids[s + 1].tile0) <= b) s++;
+    vsel = s;
+  }
+  __syncthreads();
+  v = vsel;
+  const int* src = reinterpret_cast<const int*>(vids + v);
+  int* dst = reinterpret_cast<int*>(&mv);
+  for (int i = tid; i < (int)(sizeof(MultiVideo) / sizeof(int)); i += nth) dst[i] = src[i];
+  __syncthreads();
+  return b - (UPD ? mv.upd0 : mv.tile0);
+}
+
+// Operator step `it` of every video in vids (the work of k_apply, mode 0): block
+// b works on tile b - tile0 of its video, with that video's tensor maps
+// maps[2 v], maps[2 v + 1] (global memory) and its vector step's nupd partials.
+template <int K, int TH>
+__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
+    k_apply_multi(const MultiVideo* __restrict__ vids, int nv, const CUtensorMap* __restrict__ maps, int first,
+                  int it) {
+  extern __shared__ __align__(128) float4 apply_smem[];
+  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
+  __shared__ ColorTable<K> ct;
+  __shared__ MultiVideo mv;
+  int v;
+  const int local = multi_video<false>(vids, nv, mv, v);
+  const Params& P = mv.P;
+  load_colors<K>(ct, P.col);
+  const int x0 = (local % mv.ntx) * VTW, y0 = (local / mv.ntx) * TH;
+  prefetch_tile<K, TH>(P, x0, y0);
+  const double rho_share = first ? 0.0 : part_share(pcg_partials(P, PART_RZ, it - 1), mv.nupd);
+  auto get_beta = [&]() -> float {
+    if (first) return 0.f;
+    const double rho = block_total(rho_share), rho_old = P.sc->rho2[(it - 1) & 1];
+    if (tid_flat() == 0 && local == 0) P.sc->rho2[it & 1] = rho;
+    return rho_old != 0.0 ? (float)(rho / rho_old) : 0.f;
+  };
+  float* p = const_cast<float*>(mv.p);
+  const float pq = apply_tile<K, TH>(P, t, ct, x0, y0, 0, first, get_beta, p, p, P.q, maps + 2 * v, maps + 2 * v + 1);
+  const double bs = block_sum_f(pq);
+  if (tid_flat() == 0) pcg_partials(P, PART_PQ, it)[local] = bs;
+}
+
+// Vector step `it` of every video in vids (the work of k_update): block b is
+// block b - upd0 of its video's nupd blocks.
+template <int K>
+__global__ void __launch_bounds__(256, 2) k_update_multi(const MultiVideo* __restrict__ vids, int nv, int it, int last) {
+  __shared__ MultiVideo mv;
+  int v;
+  const int local = multi_video<true>(vids, nv, mv, v);
+  const Params& P = mv.P;
+  const double pq = block_total(part_share(pcg_partials(P, PART_PQ, it), mv.ntiles));
+  const float alpha = pq != 0.0 ? (float)(P.sc->rho2[it & 1] / pq) : 0.f;
+  const float rz =
+      update_range<K>(P, mv.p, alpha, last, (long)local * blockDim.x + threadIdx.x, (long)mv.nupd * blockDim.x);
+  if (last) return;
+  const double bs = block_sum_f(rz);
+  if (threadIdx.x == 0) pcg_partials(P, PART_RZ, it)[local] = bs;
+}
+
 // ---------------------------------------------------------------- block-Jacobi preconditioner
 
 // Sec. 6.1 names no preconditioner.  Besides the Jacobi default this file offers

@@ -40,6 +40,7 @@ EXPORTS = (
     "gid_set_pcg_history",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
     "gid_batch_set_frames", "gid_batch_init", "gid_batch_new_sequence", "gid_batch_run", "gid_batch_autotune",
+    "gid_batch_set_worklist",
     "gid_net_create", "gid_net_destroy", "gid_net_last_error", "gid_net_num_params", "gid_net_launch_count",
     "gid_net_set_weights", "gid_net_get_weights", "gid_net_get_grads", "gid_net_forward", "gid_net_backward",
     "gid_net_adam_step", "gid_net_set_loss_weights", "gid_init_learned", "gid_base_color_step",
@@ -128,6 +129,7 @@ def load():
     L.gid_batch_new_sequence.argtypes = [P]
     L.gid_batch_run.argtypes = [P, I, I]
     L.gid_batch_autotune.argtypes = [P, ctypes.c_char_p, I]
+    L.gid_batch_set_worklist.argtypes = [P, I]
     L.gid_net_create.argtypes = [I, ctypes.POINTER(I), ctypes.c_uint64, P, ctypes.POINTER(P)]
     L.gid_net_destroy.argtypes = [P]
     L.gid_net_destroy.restype = None
@@ -631,6 +633,11 @@ class Batch:
 
     def autotune(self, cache_path=None, reps=5):
         self._chk(self.lib.gid_batch_autotune(self.h, cache_path.encode() if cache_path else None, reps))
+
+    def set_worklist(self, on: bool):
+        """True: PCG steps as work-list launches over all videos of one K (default);
+        False: one graph branch per video."""
+        self._chk(self.lib.gid_batch_set_worklist(self.h, 1 if on else 0))
 
 
 class Net:

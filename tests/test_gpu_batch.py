@@ -21,6 +21,8 @@ def cases():
 
 
 def test_batch_matches_single_contexts(tmp_path):
+    """Branch form: every video's launch sequence is its own graph branch, so
+    each video's state equals that of its own context bit for bit."""
     from paper_1908_01961_b300 import gid
     cs = cases()
     single = []
@@ -35,6 +37,7 @@ def test_batch_matches_single_contexts(tmp_path):
         single.append((s.state().cpu().numpy(), s.base_colors()))
     weights = [gid.default_weights(c.off_s, c.off_t if c.temporal else None, temporal=int(c.temporal)) for c in cs]
     b = gid.Batch([(c.H, c.W, c.K) for c in cs], weights)
+    b.set_worklist(False)
     for v, c in zip(b.videos, cs):
         v.set_base_colors(c.b_init)
         v.set_apply_tile(8)
@@ -119,3 +122,67 @@ def test_batch_matches_oracle():
         assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
         assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
         assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+# several videos per K: the work-list launches interleave their tiles and planes
+GROUPED = [dict(H=48, W=64, K=4, n_cells=12), dict(H=29, W=37, K=4, n_cells=7), dict(H=41, W=270, K=4, n_cells=9),
+           dict(H=30, W=33, K=3, n_cells=6), dict(H=75, W=131, K=3, n_cells=14)]
+
+
+def run_grouped(worklist, frames=2):
+    from paper_1908_01961_b300 import gid
+    cs = [Case(**sh, seed=20 + i, frames=frames, temporal=(i % 2 == 0)) for i, sh in enumerate(GROUPED)]
+    weights = [gid.default_weights(c.off_s, c.off_t if c.temporal else None, temporal=int(c.temporal)) for c in cs]
+    b = gid.Batch([(c.H, c.W, c.K) for c in cs], weights)
+    b.set_worklist(worklist)
+    for v, c in zip(b.videos, cs):
+        v.set_base_colors(c.b_init)
+        v.set_apply_tile(17)
+    out = []
+    for t in range(frames):
+        ins = [c.gpu_inputs(t) for c in cs]
+        b.set_frames([i[0] for i in ins], [i[1] for i in ins])
+        b.init(0 if t == 0 else 1)
+        b.run(3, 6)
+        out.append([(v.state().cpu().numpy().astype(np.float64), v.base_colors().astype(np.float64), v.energy()[0])
+                    for v in b.videos])
+    return cs, out
+
+
+def test_worklist_matches_branch_form_and_oracle():
+    """Five videos in two K groups (4, 4, 4 and 3, 3; ragged tiles in both
+    directions, one video 270 px wide): the work-list form against the branch
+    form with 17-row tiles (same arithmetic up to the grouping of the FP32
+    reduction partials: state within 1e-3, energy within 1e-4 relative) and
+    every video of both frames against the oracle (frame 1 from the GPU's own
+    frame-0 state): layers within 1e-3 max-abs, energy within 1e-4 relative."""
+    cs, wl = run_grouped(True)
+    _, br = run_grouped(False)
+    for t in range(2):
+        for (Xw, bw, Ew), (Xb, bb, Eb) in zip(wl[t], br[t]):
+            assert np.abs(Xw - Xb).max() <= 1e-3
+            assert np.abs(bw - bb).max() <= 1e-3
+            assert Ew == pytest.approx(Eb, rel=1e-4)
+    for i, c in enumerate(cs):
+        pb = c.oracle_problem(0)
+        Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), 3, 6)
+        X, bc, E = wl[0][i]
+        assert np.abs(np.exp(X[:3]) - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(X[3:] - Xo[3:]).max() <= 1e-3
+        assert np.abs(bc - bo).max() <= 1e-3
+        assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+        pb = c.oracle_problem(1, rprev=X[:3], b=bc) if c.temporal else c.oracle_problem(1, b=bc)
+        Xo, bo, hist = O.solve_frame(pb, X, 3, 6)
+        X1, _, E1 = wl[1][i]
+        assert np.abs(np.exp(X1[:3]) - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(X1[3:] - Xo[3:]).max() <= 1e-3
+        assert E1 == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+def test_worklist_is_reproducible():
+    """Fixed block-to-work assignment and fixed-order reductions: two runs of
+    the work-list form give the same bits."""
+    _, a = run_grouped(True, frames=1)
+    _, b = run_grouped(True, frames=1)
+    for (Xa, ba, _), (Xb, bb, _) in zip(a[0], b[0]):
+        assert np.array_equal(Xa, Xb) and np.array_equal(ba, bb)
