@@ -49,9 +49,9 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the editing, clustering, correction and preconditioner measurements (profiling runs)")
-    ap.add_argument("--tile", type=int, default=None, choices=[-1, 0, 2, 4, 8, 17],
+    ap.add_argument("--tile", type=int, default=None, choices=[-1, 0, 2, 4, 8, 17, 258, 260, 264, 273],
                     help="PCG loop instead of autotuning: operator tile rows, 0 = persistent kernel, "
-                         "-1 = resident kernel; for profiling")
+                         "-1 = resident kernel, rows + 256 = fused step; for profiling")
     ap.add_argument("--parity", action="store_true",
                     help="stream workload: after the timed run, per-layer error of 10 sampled frames against the "
                          "oracle (each solved from the GPU's state at the previous frame; minutes of host time)")
@@ -174,11 +174,17 @@ def ncu_traffic(kernel):
         return None
 
 
-def algorithmic_bytes(kind, K, P, M, ns, nt, temporal):
+def algorithmic_bytes(kind, K, P, M, ns, nt, temporal, fused=False):
     """Minimum bytes each kernel kind moves per launch as designed (FP32 planes)."""
     V = K + 4
     NC = 10 + 3 * (K + 1) + 2 * ns  # operator coefficient planes written by k_linearize (pair weights included)
     t = 1 if temporal else 0
+    if kind == "apply" and fused:  # k_pcg_step: read z, M^-1, coefficients (+ mq_old, p_old, delta after
+        first = 5 * V + NC         # step 1); write z, mq, p (+ delta)
+        rest = 9 * V + NC
+        return 4.0 * P * ((M - 1) * rest + first) / M
+    if kind == "update" and fused:  # the last step's update only: read delta, p, X; write X
+        return 4.0 * P * 4 * V
     if kind == "apply":     # read z, coefficients (+ p_old, q_old after step 1); write p, q
         first = 3 * V + NC
         rest = 5 * V + NC
@@ -295,6 +301,8 @@ def pcg_loop_name(s, rows):
         return f"resident PCG kernel ({nb} tiles of {tw}x{th}, one per SM)"
     if rows == 0:
         return "persistent PCG kernel"
+    if rows > 0 and rows & 256:
+        return f"128x{rows & 255} tiles, one fused kernel per PCG step (vector update folded into the operator)"
     return f"128x{rows} operator tiles, operator and vector kernels per PCG step"
 
 
@@ -405,8 +413,9 @@ def run_gid(args, ws, rank, local):
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms = kinds[dom][0] / kinds[dom][1]
     peak, peak_src = measured_peaks()
-    kernel_name = {"apply": "k_apply", "update": "k_update", "linearize": "k_linearize", "dense": "k_dense",
-                   "pcg": "k_pcg_resident" if tile_rows == -1 else "k_pcg"}.get(dom)
+    fused = tile_rows > 0 and (tile_rows & 256) != 0
+    kernel_name = {"apply": "k_pcg_step" if fused else "k_apply", "update": "k_update", "linearize": "k_linearize",
+                   "dense": "k_dense", "pcg": "k_pcg_resident" if tile_rows == -1 else "k_pcg"}.get(dom)
     # The profiled step launches kernel by kernel with an event after each (no
     # graph replay, no programmatic overlap), so it runs slower than the timed
     # steps: a kind's time per step is its share of the profiled step times the
@@ -427,7 +436,7 @@ def run_gid(args, ws, rank, local):
     pcg_us = 1000.0 * pcg_ms / n_pcg
     ach = pcg_bytes / (pcg_us * 1e-6) / 1e9
     traffic = ncu_traffic("pcg_step")
-    alg = algorithmic_bytes(dom, K, P, M, len(off_s), len(off_t), True)
+    alg = algorithmic_bytes(dom, K, P, M, len(off_s), len(off_t), True, fused)
     design = None
     if alg and dom in ("apply", "update"):
         dom_scaled = dom_ms * scale
@@ -435,7 +444,9 @@ def run_gid(args, ws, rank, local):
                   "achieved_GBps": alg / (dom_scaled / 1000.0) / 1e9, "frac": alg / (dom_scaled / 1000.0) / 1e9 / peak,
                   "note": "the kernel's own design bytes (stored coefficient planes) per launch"}
     roof = {"bound": "hbm", "kernel": "PCG step (" + ("k_pcg_resident" if "pcg" in kinds and tile_rows == -1 else
-                                                      "k_pcg" if "pcg" in kinds else "k_apply + k_update") + ")",
+                                                      "k_pcg" if "pcg" in kinds else
+                                                      "k_pcg_step, last step's k_update" if fused else
+                                                      "k_apply + k_update") + ")",
             "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak, "traffic": traffic,
             "peak_source": peak_src, "algorithmic_bytes_per_step": pcg_bytes,
             "bytes_per_px": 4 * (8 * V + 2 + S_pairs), "pcg_step_us": pcg_us, "pcg_steps_per_video": n_pcg,
@@ -525,7 +536,7 @@ def run_gid(args, ws, rank, local):
         preconditioners = []
         sp = gid.Solver(H, W, K, gid.default_weights(off_s))
         sp.set_frame(rgb[0], lab[0])
-        sp.set_apply_tile(tile_rows if tile_rows and tile_rows > 0 else 17)   # one operator kernel per PCG step in both arms
+        sp.set_apply_tile((tile_rows & 255) if tile_rows and tile_rows > 0 else 17)   # one operator kernel per PCG step in both arms
         for kind in ("jacobi", "block"):
             sp.set_preconditioner(kind)
             for Mi in (10, 15, 20):
@@ -563,7 +574,7 @@ def run_gid(args, ws, rank, local):
 
         sb = gid.Solver(H, W, K, w)
         sb.set_base_colors(b0)
-        sb.set_apply_tile(tile_rows if tile_rows and tile_rows > 0 else 17)
+        sb.set_apply_tile((tile_rows & 255) if tile_rows and tile_rows > 0 else 17)
         e_ref = video_energies(s, M)
         sb.set_preconditioner("block")
         ratios, Mb = {}, None

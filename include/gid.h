@@ -253,11 +253,21 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
  * block per SM), so it exists only for frames up to a few hundred thousand
  * pixels (640 x 480 at K = 6 is 148 tiles of 160 x 13 on 148 SMs); the first
  * selection allocates its exchange buffers (V planes + 12 KB) and synchronises.
- * Jacobi preconditioner only (GID_PRECOND_BLOCK keeps the two-kernel loop).
+ * rows = 2, 4, 8 or 17 | GID_PCG_FUSED: one kernel per PCG step whose
+ * operator tile also does the previous step's vector update (for the tile and
+ * the stencil's halo, so each block computes its halo's z itself); z and M^-1 q
+ * alternate between two buffers by step parity, and the PCG scalars come from
+ * one set of block partials per step (<p, q>, <z, q>, <q, M^-1 q>: rho of the
+ * next step by the expanded recurrence instead of a second reduction).  Fewer
+ * bytes per step than the two-kernel loop (no separate pass over the PCG
+ * vectors); the first selection allocates 2 V planes and synchronises.
+ * Jacobi preconditioner only for the single-launch and fused loops
+ * (GID_PRECOND_BLOCK keeps the two-kernel loop).
  * GID_ERR_INVALID_ARG if the device cannot co-schedule the chosen loop or the
- * frame does not fit.  Results agree to FP32 rounding order; only speed
- * differs. */
+ * frame does not fit; GID_ERR_OOM if a loop's buffers cannot be allocated.
+ * Results agree to FP32 rounding order; only speed differs. */
 #define GID_PCG_RESIDENT (-1)
+#define GID_PCG_FUSED 256
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
 /* The context's PCG loop (*rows as passed to gid_set_apply_tile) and the tile
@@ -324,16 +334,17 @@ int gid_set_preconditioner(gid_ctx* ctx, int kind);
 /* The context's preconditioner (GID_PRECOND_*), -1 for a NULL ctx. */
 int gid_get_preconditioner(const gid_ctx* ctx);
 
-/* Time reps PCG steps with each of the six ways above on the current frame
+/* Time reps PCG steps with each of the ten ways above on the current frame
  * and state (CUDA events on the context stream) and keep the fastest.  Writes
- * the chosen rows (0 = persistent, GID_PCG_RESIDENT) to *rows_out and the six
- * timings (us per PCG step; shapes 2, 4, 8, 17, persistent, resident, -1 if
- * unavailable) to us_out[GID_AUTOTUNE_TIMINGS]; either may be NULL.  The single-launch loops are
- * timed as the difference of two Gauss-Newton steps (reps + 2 and 2 PCG
- * steps), so that the linearisation does not count.  Needs gid_set_frame and a state; leaves the state X
+ * the chosen rows (0 = persistent, GID_PCG_RESIDENT, rows | GID_PCG_FUSED) to
+ * *rows_out and the ten timings (us per PCG step; shapes 2, 4, 8, 17,
+ * persistent, resident, fused 2, 4, 8, 17; -1 if unavailable) to
+ * us_out[GID_AUTOTUNE_TIMINGS]; either may be NULL.  The single-launch and
+ * fused loops are timed as the difference of two Gauss-Newton steps (reps + 2
+ * and 2 PCG steps), so that the linearisation does not count.  Needs gid_set_frame and a state; leaves the state X
  * unchanged (the PCG vectors are scratch until the next gid_run).  Call it
  * between runs.  Synchronises. */
-#define GID_AUTOTUNE_TIMINGS 6
+#define GID_AUTOTUNE_TIMINGS 10
 int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
 
 /* ---- batches of videos (many videos of uneven size, one graph per step) ---- */

@@ -60,6 +60,8 @@ struct gid_ctx {
   int dense_cap = 148;     // base-colour-step blocks resident at once
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
   bool resident = false;   // resident PCG kernel selected (gid_set_apply_tile(-1) / gid_autotune)
+  bool fused = false;      // one-kernel PCG step selected (gid_set_apply_tile(rows | GID_PCG_FUSED))
+  float* fbuf = nullptr;   // its odd-step z and M^-1 q buffers (2 x V planes, allocated on first use)
   ResTile res{};           // its tile geometry; res_blocks = 0 if the frame does not fit on chip
   CUtensorMap res_map;     // its coefficient stream: box [1 plane][TH + 1 rows][4 TX + 8 columns]
   int res_blocks = 0, res_threads = 0;
@@ -201,9 +203,11 @@ static Params params(const gid_ctx* c) {
 
 // How the PCG loop of a Gauss-Newton step runs: 0 one operator and one vector
 // kernel per step, 1 the persistent cooperative kernel, 2 the resident one.
+// 0: operator and vector kernel per PCG step; 1: persistent; 2: resident; 3: fused step
 static int pcg_kernel(const gid_ctx* c) {
   if (c->resident && c->res_blocks > 0) return 2;
   if (c->persistent && c->pcg_blocks > 0) return 1;
+  if (c->fused && c->fbuf) return 3;
   return 0;
 }
 
@@ -306,8 +310,42 @@ struct Launch {
     launch_pdl(c, k_apply<K, TH>, grid, dim3(BX, TH), smem, params(c), mode, first, it, vector_blocks(c), pin, pout,
                qout, m->r, m->t);
   }
+  // Fused PCG step `it` (k_pcg_step): z and M^-1 q alternate between the
+  // context's buffers (z, q) for even steps and fbuf for odd ones.
+  template <int TH>
+  static void pcg_step_th(const gid_ctx* c, int it) {
+    float* zb[2] = {c->z, c->fbuf};
+    float* mb[2] = {c->q, c->fbuf + (long)c->V * c->plane};
+    const float* zin = zb[(it - 1) & 1];
+    const float* mqin = mb[(it - 1) & 1];
+    const gid_ctx::Maps* m = tile_maps(const_cast<gid_ctx*>(c), zin, TH);
+    const gid_ctx::Maps* mq = tile_maps(const_cast<gid_ctx*>(c), mqin, TH);
+    if (!m || !mq) {
+      const_cast<gid_ctx*>(c)->map_failed = true;
+      return;
+    }
+    const dim3 grid((c->W + VTW - 1) / VTW, (c->H + TH - 1) / TH);
+    launch_pdl(c, k_pcg_step<K, TH>, grid, dim3(BX, TH), fused_smem_bytes<K, TH>(), params(c), it, apply_blocks(c),
+               zin, zb[it & 1], mqin, mb[it & 1], c->pA, m->r, m->t, mq->r, mq->t);
+  }
+  static void pcg_step(const gid_ctx* c, int it) {
+    switch (c->apply_th) {
+      case 2: pcg_step_th<2>(c, it); break;
+      case 4: pcg_step_th<4>(c, it); break;
+      case 17: pcg_step_th<17>(c, it); break;
+      default: pcg_step_th<8>(c, it); break;
+    }
+  }
   // Opt every operator tile shape in to its dynamic shared memory (before any graph capture).
   static void prepare(const gid_ctx*) {
+    cudaFuncSetAttribute(k_pcg_step<K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem_bytes<K, 2>());
+    cudaFuncSetAttribute(k_pcg_step<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem_bytes<K, 4>());
+    cudaFuncSetAttribute(k_pcg_step<K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem_bytes<K, 8>());
+    cudaFuncSetAttribute(k_pcg_step<K, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fused_smem_bytes<K, 17>());
     cudaFuncSetAttribute(k_apply<K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 2>));
     cudaFuncSetAttribute(k_apply<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 4>));
     cudaFuncSetAttribute(k_apply<K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 8>));
@@ -620,7 +658,7 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
   const size_t pbytes = (size_t)npart * sizeof(double);
   c->nbmax = (int)std::max({(long)update_blocks(c), (long)((W + VTW - 1) / VTW) * ((H + 1) / 2), 148L * 32});
-  const size_t ppbytes = sizeof(double) * 4 * (size_t)c->nbmax;
+  const size_t ppbytes = sizeof(double) * 2 * PART_KINDS * (size_t)c->nbmax;
   c->pool_bytes = fbytes + lbytes + 256 * 9 + sizeof(DevColors) + sizeof(DevScalars) + pbytes + ppbytes;
   e = cudaMalloc(&c->pool, c->pool_bytes);
   if (e != cudaSuccess) {
@@ -707,6 +745,7 @@ extern "C" void gid_destroy(gid_ctx* c) {
   cudaFree(c->pool);
   cudaFree(c->blk);
   cudaFree(c->zx);
+  cudaFree(c->fbuf);
   cudaFree(c->xval);
   cudaFree(c->st_rgb);
   cudaFree(c->st_lab);
@@ -855,7 +894,7 @@ static void record_rho(gid_ctx* c, int m) {
 
 static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   c->last_m_inner = m_inner;
-  c->hist_valid = c->record_rho || (pcg_kernel(c) != 0 && c->precond == GID_PRECOND_JACOBI);
+  c->hist_valid = c->record_rho || (pcg_kernel(c) != 0 && c->precond == GID_PRECOND_JACOBI);  // in-kernel history
   if (c->precond == GID_PRECOND_BLOCK) {
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 3, (float*)nullptr, (float*)nullptr); });
     launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, block_factor, c); });
@@ -871,6 +910,12 @@ static int enqueue_gn_step(gid_ctx* c, int m_inner, int last_mode) {
   }
   launch(c, GID_KIND_LINEARIZE, [&] { GID_DISPATCH(c, linearize, c, 0, (float*)nullptr, (float*)nullptr); });
   if (int rc = check_launch(c, "k_linearize")) return rc;
+  if (pcg_kernel(c) == 3) {
+    // one fused kernel per PCG step, then the last step's vector update
+    for (int m = 1; m <= m_inner; m++) launch(c, GID_KIND_APPLY, [&] { GID_DISPATCH(c, pcg_step, c, m); });
+    launch(c, GID_KIND_UPDATE, [&] { GID_DISPATCH(c, update, c, m_inner, (const float*)c->pA, last_mode); });
+    return check_launch(c, "k_pcg_step");
+  }
   if (pcg_kernel(c) == 2) {
     cudaError_t e = cudaSuccess;
     launch(c, GID_KIND_PCG, [&] {
@@ -1311,6 +1356,20 @@ static int res_prepare(gid_ctx* c) {
   return GID_OK;
 }
 
+// The fused PCG step's odd-step buffers (allocated once, zeroed: their padding
+// columns stay zero like those of every PCG vector).
+static int fused_prepare(gid_ctx* c) {
+  if (c->fbuf) return GID_OK;
+  const size_t bytes = sizeof(float) * 2 * (size_t)c->V * c->plane;
+  if (cudaMalloc(&c->fbuf, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    c->fbuf = nullptr;
+    return fail(c, GID_ERR_OOM, "cudaMalloc of the fused PCG step's buffers");
+  }
+  GID_TRY_CUDA(c, cudaMemsetAsync(c->fbuf, 0, bytes, c->stream));
+  return GID_OK;
+}
+
 extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   if (rows == GID_PCG_RESIDENT) {
@@ -1325,18 +1384,24 @@ extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
     c->resident = false;
     return GID_OK;
   }
+  const bool fused = rows > 0 && (rows & GID_PCG_FUSED);
+  if (fused) rows &= ~GID_PCG_FUSED;
   if (rows != 2 && rows != 4 && rows != 8 && rows != 17)
-    return fail(c, GID_ERR_INVALID_ARG, "tile rows must be -1 (resident), 0 (persistent), 2, 4, 8 or 17");
+    return fail(c, GID_ERR_INVALID_ARG,
+                "tile rows must be -1 (resident), 0 (persistent), 2, 4, 8 or 17 (optionally | GID_PCG_FUSED)");
+  if (fused)
+    if (int rc = fused_prepare(c)) return rc;
   c->apply_th = rows;
   c->persistent = false;
   c->resident = false;
+  c->fused = fused;
   return GID_OK;
 }
 
 extern "C" int gid_get_pcg_layout(gid_ctx* c, int* rows, int* tile_w, int* tile_h, int* blocks) {
   if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
   const int k = pcg_kernel(c);
-  if (rows) *rows = k == 2 ? GID_PCG_RESIDENT : (k == 1 ? 0 : c->apply_th);
+  if (rows) *rows = k == 2 ? GID_PCG_RESIDENT : (k == 1 ? 0 : (k == 3 ? c->apply_th | GID_PCG_FUSED : c->apply_th));
   if (!c->res_planned) GID_DISPATCH(c, res_plan, c);
   if (tile_w) *tile_w = c->res_blocks > 0 ? 4 * c->res.TX : 0;
   if (tile_h) *tile_h = c->res_blocks > 0 ? c->res.TH : 0;
@@ -1441,6 +1506,8 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
   float best = 1e30f;
   int best_th = c->apply_th;
   c->persistent = false;
+  c->resident = false;
+  c->fused = false;
   for (int i = 0; i < 4; i++) {
     c->apply_th = cand[i];
     int it = 0;
@@ -1483,8 +1550,9 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
     *us = 1000.f * (ms[1] - ms[0]) / reps;
     return sync_status(c);
   };
-  int choice = best_th;  // rows, 0 persistent, GID_PCG_RESIDENT resident
+  int choice = best_th;  // rows, 0 persistent, GID_PCG_RESIDENT resident, rows | GID_PCG_FUSED
   c->resident = false;
+  c->fused = false;
   if (c->pcg_blocks > 0) {
     c->persistent = true;
     float us = 0.f;
@@ -1511,6 +1579,25 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
   } else if (us_out) {
     us_out[5] = -1.f;
   }
+  // the fused step (one kernel per PCG step) with each tile shape
+  const int th_tiled = c->apply_th;
+  for (int i = 0; i < 4; i++) {
+    if (c->precond != GID_PRECOND_JACOBI || fused_prepare(c) != GID_OK) {
+      if (us_out) us_out[6 + i] = -1.f;
+      continue;
+    }
+    c->fused = true;
+    c->apply_th = cand[i];
+    float us = 0.f;
+    if (int rc = time_loop(&us)) return rc;
+    if (us_out) us_out[6 + i] = us;
+    if (us < best) {
+      best = us;
+      choice = cand[i] | GID_PCG_FUSED;
+    }
+  }
+  c->fused = choice > 0 && (choice & GID_PCG_FUSED);
+  c->apply_th = c->fused ? (choice & ~GID_PCG_FUSED) : th_tiled;
   c->persistent = choice == 0;
   c->resident = choice == GID_PCG_RESIDENT;
   cudaEventDestroy(e0);

@@ -201,7 +201,9 @@ __device__ __forceinline__ double grid_total(const double* partial, int n, int s
 __device__ __forceinline__ double* pcg_partials(const Params& P, int kind, int it) {
   return P.pcg_part + ((long)kind * 2 + (it & 1)) * P.nbmax;
 }
-enum { PART_PQ = 0, PART_RZ = 1 };
+// kinds: <p, q> (operator step), <r, z> (vector step); the fused PCG step
+// (k_pcg_step) uses <p, q>, <z, q> in the second kind's slots and <q, M^-1 q>
+enum { PART_PQ = 0, PART_RZ = 1, PART_ZQ = 1, PART_QMQ = 2, PART_KINDS = 3 };
 
 // ---------------------------------------------------------------- IRLS weights (Sec. 5.3)
 
@@ -964,18 +966,15 @@ __device__ __forceinline__ void grid_dep_release() { asm volatile("griddepcontro
 // With mapR / mapT (tensor maps of the staged vector, boxes [3][TH + 6][136] and
 // [K + 1][TH + 2][136]) the tile is staged by TMA; without them (nullptr) by
 // per-thread asynchronous copies.
-template <int K, int TH, class GB>
-__device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t, const ColorTable<K>& ct, int x0, int y0,
-                                            int mode, int first, GB get_beta, const float* pin, float* pout,
-                                            float* __restrict__ qout, const CUtensorMap* mapR = nullptr,
-                                            const CUtensorMap* mapT = nullptr) {
-  constexpr int NCH = VRW / 4;  // float4 chunks per staged row
-  constexpr int NTH = BX * TH;  // threads per block
-  const int tid = tid_flat();
-  // Stage s = z (PCG step) or s = pin (stage call) with its halo.
-  const float* __restrict__ sv = mode == 0 ? P.z : pin;
-  constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH;
-  auto chunk_dst = [&](int i, int& gy, int& gx, int& v) -> float* {
+// Staged chunk i of an operator tile (origin x0, y0): its shared address, its
+// plane v and the frame position (gy, gx) of its first float.  Chunks run over
+// the reflectance channels' rows y0 - 3 .. y0 + TH + 2, then the layers' rows
+// y0 - 1 .. y0 + TH, each row in float4 columns x0 - 4 .. x0 + 131.
+template <int K, int TH>
+struct TileChunks {
+  static constexpr int NCH = VRW / 4;  // float4 chunks per staged row
+  static constexpr int NR = 3 * (TH + 2 * AHR) * NCH, NTOT = NR + (K + 1) * (TH + 2) * NCH;
+  __device__ __forceinline__ static float* at(ApplyTile<K, TH>& t, int x0, int y0, int i, int& gy, int& gx, int& v) {
     if (i < NR) {
       const int c = i / ((TH + 2 * AHR) * NCH), rem = i - c * (TH + 2 * AHR) * NCH, ly = rem / NCH, lc = rem - ly * NCH;
       gy = y0 - AHR + ly;
@@ -988,7 +987,23 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
     gx = x0 - VHX + 4 * lc;
     v = 3 + k;
     return &t.pt[k][ly][4 * lc];
-  };
+  }
+};
+
+// Stage the V planes at sv (tile and halo, zero outside the frame) into t:
+// by TMA with mapR / mapT (tensor maps of sv, boxes [3][TH + 6][136] and
+// [K + 1][TH + 2][136]), else by per-thread asynchronous copies.  False in every
+// thread if the TMA copy did not complete within the bounded wait (ST_TIMEOUT
+// is recorded and the copy still in flight gets a second bounded wait); the
+// caller then skips the tile's arithmetic and stores.  All threads call; the
+// staged tile is visible to the whole block on return.
+template <int K, int TH>
+__device__ __forceinline__ bool stage_tile(const Params& P, ApplyTile<K, TH>& t, int x0, int y0,
+                                           const float* __restrict__ sv, const CUtensorMap* mapR,
+                                           const CUtensorMap* mapT) {
+  using TC = TileChunks<K, TH>;
+  constexpr int NTH = BX * TH;  // threads per block
+  const int tid = tid_flat();
   const bool use_tma = mapR != nullptr && ((smem_addr(&t.pr[0][0][0]) | smem_addr(&t.pt[0][0][0])) & 127u) == 0u;
   if (use_tma) {
     // two TMA boxes (reflectance channels with a 3-row halo, layers with 1),
@@ -1005,26 +1020,36 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
     bool done = false;
     for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
     if (!__syncthreads_and(done)) {
-      // the copy did not complete in time: record it, give the copy still in
-      // flight into this block's shared memory a second bounded wait, and leave
-      // p and q unwritten (the status makes the next synchronising call fail)
+      // the copy did not complete in time: record it and give the copy still
+      // in flight into this block's shared memory a second bounded wait (the
+      // status makes the next synchronising call fail)
       if (tid == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
       for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
-      return 0.f;
+      return false;
     }
   } else {
     // Every chunk is an asynchronous 16-byte copy straight into shared memory
     // (zero-filled outside the frame): all of a thread's copies are in flight
     // at once and hold no registers.
-    for (int i = tid; i < NTOT; i += NTH) {
+    for (int i = tid; i < TC::NTOT; i += NTH) {
       int gy, gx, v;
-      float* dst = chunk_dst(i, gy, gx, v);
+      float* dst = TC::at(t, x0, y0, i, gy, gx, v);
       const bool ok = gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch;
       cp_async16(dst, ok ? sv + v * P.plane + off2(P, gy, gx) : sv, ok ? 16 : 0);
     }
     cp_async_wait_all();
   }
   __syncthreads();
+  return true;
+}
+
+template <int K, int TH, class GB>
+__device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t, const ColorTable<K>& ct, int x0, int y0,
+                                            int mode, int first, GB get_beta, const float* pin, float* pout,
+                                            float* __restrict__ qout, const CUtensorMap* mapR = nullptr,
+                                            const CUtensorMap* mapT = nullptr) {
+  // Stage s = z (PCG step) or s = pin (stage call) with its halo.
+  if (!stage_tile<K, TH>(P, t, x0, y0, mode == 0 ? P.z : pin, mapR, mapT)) return 0.f;
   const float beta = get_beta();
   float pq = 0.f;
   const int y = y0 + threadIdx.y, x = x0 + QW * threadIdx.x;
@@ -2186,6 +2211,194 @@ __global__ void __launch_bounds__(RES_MAXT, 1)
     rho = rho_new;
     if (blockIdx.x == 0 && tid == 0 && m < PCG_HIST) P.sc->rho_hist[m] = rho;
     __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------- fused PCG step
+
+// One launch per PCG step (Sec. 6.1's PCG, Jacobi preconditioner), the vector
+// step of step it - 1 folded into the operator step it.  Step it - 1 left
+// z_(it-1) (buffer zin), mq_(it-1) = M^-1 q_(it-1) (buffer mqin), p_(it-1) and
+// the block partials of <p, q>, <z, q>, <q, M^-1 q>.  Every block forms from
+// those, in the same fixed order,
+//   alpha = rho_(it-1) / <p, q>,
+//   rho_it = rho_(it-1) - 2 alpha <z, q> + alpha^2 <q, M^-1 q>   (<r_it, z_it>
+//            with r_it = r - alpha q, z_it = z - alpha M^-1 q, expanded),
+//   beta = rho_it / rho_(it-1),
+// stages z_(it-1) and mq_(it-1) with the stencil's halo (two TMA tiles),
+// turns every staged value into z_it = z_(it-1) - alpha mq_(it-1) (the halo's
+// owners compute the same values by the same operation), applies A = J^T J to
+// it, and at its own pixels forms q_it = A z_it + beta q_(it-1) (q_(it-1) =
+// mq_(it-1) / M^-1), p_it = z_it + beta p_(it-1) and delta += alpha p_(it-1),
+// writing z_it to zout, M^-1 q_it to mqout, p_it and delta in place.  Step 1
+// (it == 1) starts from the PCG start: z_1 = z, p_1 = z, beta = 0, delta
+// untouched (zero).  zin / zout and mqin / mqout alternate by step parity:
+// neighbouring blocks read the old vectors' halo while this block writes the
+// new ones.  The last step's delta += alpha p (and X += delta) is the vector
+// step of k_update.  mapR / mapT and mapRq / mapTq: tensor maps of zin and
+// mqin.  Where two tiles do not fit in shared memory (MQS false) mq_(it-1) is
+// read from global memory, four chunks in flight per thread.
+template <int K, int TH>
+constexpr bool fused_mq_staged() {
+  return 2 * sizeof(ApplyTile<K, TH>) + 4096 <= 227 * 1024;
+}
+
+template <int K, int TH>
+constexpr size_t fused_smem_bytes() {
+  return (fused_mq_staged<K, TH>() ? 2 : 1) * sizeof(ApplyTile<K, TH>);
+}
+
+template <int K, int TH>
+__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
+    k_pcg_step(Params P, int it, int nb_prev, const float* __restrict__ zin, float* __restrict__ zout,
+               const float* __restrict__ mqin, float* __restrict__ mqout, float* __restrict__ p,
+               const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapT,
+               const __grid_constant__ CUtensorMap mapRq, const __grid_constant__ CUtensorMap mapTq) {
+  using TC = TileChunks<K, TH>;
+  constexpr int NTH = BX * TH;
+  constexpr bool MQS = fused_mq_staged<K, TH>();
+  extern __shared__ __align__(128) float4 apply_smem[];
+  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
+  ApplyTile<K, TH>& tq = *(reinterpret_cast<ApplyTile<K, TH>*>(apply_smem) + (MQS ? 1 : 0));
+  __shared__ ColorTable<K> ct;
+  load_colors<K>(ct, P.col);
+  const int x0 = blockIdx.x * VTW, y0 = blockIdx.y * TH, tid = tid_flat();
+  prefetch_tile<K, TH>(P, x0, y0);
+  grid_dep_wait();
+  grid_dep_release();
+  const bool first = it == 1;
+  double sh_pq = 0.0, sh_zq = 0.0, sh_qmq = 0.0;
+  if (!first) {
+    sh_pq = part_share(pcg_partials(P, PART_PQ, it - 1), nb_prev);
+    sh_zq = part_share(pcg_partials(P, PART_ZQ, it - 1), nb_prev);
+    sh_qmq = part_share(pcg_partials(P, PART_QMQ, it - 1), nb_prev);
+  }
+  const bool two = MQS && !first;
+  if (((smem_addr(&t.pr[0][0][0]) | smem_addr(&t.pt[0][0][0]) | smem_addr(&tq.pr[0][0][0]) |
+        smem_addr(&tq.pt[0][0][0])) & 127u) != 0u) {
+    // TMA destinations must be 128-byte aligned: per-thread asynchronous copies instead
+    for (int i = tid; i < (two ? 2 : 1) * TC::NTOT; i += NTH) {
+      int gy, gx, v;
+      const bool sec = i >= TC::NTOT;
+      float* dst = TC::at(sec ? tq : t, x0, y0, sec ? i - TC::NTOT : i, gy, gx, v);
+      const float* src = sec ? mqin : zin;
+      const bool ok = gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch;
+      cp_async16(dst, ok ? src + v * P.plane + off2(P, gy, gx) : src, ok ? 16 : 0);
+    }
+    cp_async_wait_all();
+    __syncthreads();
+  } else {
+    // z_(it-1) and (after step 1, in shared memory) mq_(it-1): one barrier for all boxes
+    __shared__ __align__(8) uint64_t bar;
+    if (tid == 0) mbar_init(&bar, 1);
+    __syncthreads();
+    if (tid == 0) {
+      mbar_expect_tx(&bar, (unsigned)((two ? 2 : 1) * (sizeof(t.pr) + sizeof(t.pt))));
+      tma_load_3d(&t.pr[0][0][0], &mapR, x0 - VHX, y0 - AHR, 0, &bar);
+      tma_load_3d(&t.pt[0][0][0], &mapT, x0 - VHX, y0 - 1, 3, &bar);
+      if (two) {
+        tma_load_3d(&tq.pr[0][0][0], &mapRq, x0 - VHX, y0 - AHR, 0, &bar);
+        tma_load_3d(&tq.pt[0][0][0], &mapTq, x0 - VHX, y0 - 1, 3, &bar);
+      }
+    }
+    bool done = false;
+    for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
+    if (!__syncthreads_and(done)) {
+      // record the timeout, give the copies still in flight a second bounded
+      // wait and write nothing (the status fails the next synchronising call)
+      if (tid == 0) atomicOr(&P.sc->status, ST_TIMEOUT);
+      for (long i = 0; i < TMA_SPINS && !done; i++) done = mbar_try_wait(&bar, 0);
+      return;
+    }
+  }
+  float alpha = 0.f, beta = 0.f;
+  if (!first) {
+    const double pq = block_total(sh_pq), zq = block_total(sh_zq), qmq = block_total(sh_qmq);
+    const double rho = P.sc->rho2[(it - 1) & 1];
+    const double ad = pq != 0.0 ? rho / pq : 0.0;
+    const double rho_new = rho - 2.0 * ad * zq + ad * ad * qmq;
+    alpha = (float)ad;
+    beta = rho != 0.0 ? (float)(rho_new / rho) : 0.f;
+    if (tid == 0 && blockIdx.x == 0 && blockIdx.y == 0) {
+      P.sc->rho2[it & 1] = rho_new;
+      if (it - 1 < PCG_HIST) P.sc->rho_hist[it - 1] = rho_new;
+    }
+    // z_it over the staged tile and halo (outside the frame both tiles read zero)
+    auto zstep = [&](float* zs, float4 mq) {
+      const float4 z = *reinterpret_cast<const float4*>(zs);
+      *reinterpret_cast<float4*>(zs) = make_float4(fmaf(-alpha, mq.x, z.x), fmaf(-alpha, mq.y, z.y),
+                                                   fmaf(-alpha, mq.z, z.z), fmaf(-alpha, mq.w, z.w));
+    };
+    if constexpr (MQS) {
+      // the two tiles have one layout: walk both as float4 arrays (padding included)
+      float4* zf = reinterpret_cast<float4*>(&t);
+      const float4* mf = reinterpret_cast<const float4*>(&tq);
+      for (int i = tid; i < (int)(sizeof(ApplyTile<K, TH>) / 16); i += NTH) zstep(reinterpret_cast<float*>(zf + i), mf[i]);
+    } else {
+      constexpr int U = 4;
+      for (int i0 = tid; i0 < TC::NTOT; i0 += U * NTH) {
+        float4 mq[U];
+        float* zs[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+          int gy, gx, v;
+          const int i = i0 + u * NTH;
+          zs[u] = nullptr;
+          if (i < TC::NTOT) {
+            float* a = TC::at(t, x0, y0, i, gy, gx, v);
+            if (gy >= 0 && gy < P.H && gx >= 0 && gx < P.pitch) {
+              zs[u] = a;
+              mq[u] = *reinterpret_cast<const float4*>(mqin + v * P.plane + off2(P, gy, gx));
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++)
+          if (zs[u]) zstep(zs[u], mq[u]);
+      }
+    }
+    __syncthreads();
+  }
+  float pq = 0.f, zq = 0.f, qmq = 0.f;
+  const int y = y0 + threadIdx.y, x = x0 + QW * threadIdx.x;
+  if (x < P.W && y < P.H) {
+    const long o = off2(P, y, x);
+    const long PL = P.plane;
+    const F4 bb = f4s(beta), aa = f4s(alpha);
+    const int cx = VHX + QW * threadIdx.x, ry = threadIdx.y + AHR, ty = threadIdx.y + 1;
+    // lanes past the frame's right edge: z, M^-1, p, delta and mq are zero there and stay zero
+    auto finish = [&](int v, F4 s, F4 q) {
+      const long ov = v * PL + o;
+      const F4 mi = ldc4(P.Minv + ov);
+      F4 pn = s;
+      if (!first) {
+        const F4 mo = MQS ? lds4(v < 3 ? &tq.pr[v][ry][cx] : &tq.pt[v - 3][ty][cx]) : ldg4(mqin + ov);
+        const F4 qo = f4v(mi.a.x > 0.f ? __fdividef(mo.a.x, mi.a.x) : 0.f, mi.a.y > 0.f ? __fdividef(mo.a.y, mi.a.y) : 0.f,
+                          mi.b.x > 0.f ? __fdividef(mo.b.x, mi.b.x) : 0.f, mi.b.y > 0.f ? __fdividef(mo.b.y, mi.b.y) : 0.f);
+        const F4 po = ldg4(p + ov);
+        pn = fma4(bb, po, s);
+        q = fma4(bb, qo, q);
+        float4* dv = reinterpret_cast<float4*>(P.d + ov);
+        *dv = to4(fma4(aa, po, f4(*dv)));
+      }
+      const F4 mq = mul4(mi, q);
+      *reinterpret_cast<float4*>(zout + ov) = to4(s);
+      *reinterpret_cast<float4*>(mqout + ov) = to4(mq);
+      *reinterpret_cast<float4*>(p + ov) = to4(pn);
+      pq += dot4(pn, q);
+      zq += dot4(s, q);
+      qmq += dot4(q, mq);
+    };
+    op_apply4<K, TH >= 17>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
+                           VRW, finish);
+  }
+  double part[RES_NV];
+  block_sum3_f(pq, zq, qmq, part);
+  if (tid == 0) {
+    const int b = blockIdx.y * gridDim.x + blockIdx.x;
+    pcg_partials(P, PART_PQ, it)[b] = part[0];
+    pcg_partials(P, PART_ZQ, it)[b] = part[1];
+    pcg_partials(P, PART_QMQ, it)[b] = part[2];
   }
 }
 

@@ -18,6 +18,8 @@ LIB_PATH = os.path.join(HERE, "libgid.so")
 GID_OK = 0
 PRECOND_JACOBI, PRECOND_BLOCK = 0, 1
 RESIDENT = -1  # gid_set_apply_tile: the resident PCG loop (GID_PCG_RESIDENT)
+FUSED = 256    # gid_set_apply_tile(rows | FUSED): one kernel per PCG step (GID_PCG_FUSED)
+AUTOTUNE_LOOPS = (2, 4, 8, 17, 0, RESIDENT, 2 | FUSED, 4 | FUSED, 8 | FUSED, 17 | FUSED)
 ERR_TIMEOUT, ERR_NUMERIC = -5, -6
 ENERGY_TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness",
                 "non_neg")
@@ -504,12 +506,12 @@ class Solver:
         return ("jacobi", "block")[self.lib.gid_get_preconditioner(self.h)]
 
     def autotune(self, reps: int = 10):
-        """Pick the fastest PCG execution (tile rows, 0 = persistent, -1 = resident) on the
-        current frame; returns (rows, {rows: us per PCG step})."""
+        """Pick the fastest PCG execution (tile rows, 0 = persistent, -1 = resident, rows | FUSED)
+        on the current frame; returns (rows, {rows: us per PCG step})."""
         rows = ctypes.c_int()
-        us = (ctypes.c_float * 6)()
+        us = (ctypes.c_float * len(AUTOTUNE_LOOPS))()
         self._chk(self.lib.gid_autotune(self.h, reps, ctypes.byref(rows), us))
-        return rows.value, dict(zip((2, 4, 8, 17, 0, RESIDENT), us[:]))
+        return rows.value, dict(zip(AUTOTUNE_LOOPS, us[:]))
 
     def pcg_layout(self):
         """(rows of the current PCG loop, (tile_w, tile_h, blocks) of the resident loop on this
