@@ -943,7 +943,11 @@ def run_stream(args, ws, rank, local):
     stream = torch.cuda.current_stream()
     s.set_frame(rgb[0], lab[0])
     s.init(0)
-    tile_rows, tile_us = s.autotune(5)
+    if args.tile is None:
+        tile_rows, tile_us = s.autotune(5)
+    else:
+        s.set_apply_tile(args.tile)
+        tile_rows, tile_us = args.tile, "fixed by --tile"
 
     def frame(t):
         s.set_frame(rgb[t], lab[t])
@@ -982,7 +986,8 @@ def run_stream(args, ws, rank, local):
                "config": {"workload": f"stream_1920x1080_K8: {F} frames, 80 moving Voronoi cells, rotating light; "
                                       "frame 0 cold, then warm starts with temporal pairs", "H": H, "W": W, "K": K,
                           "frames": F, "N_outer": N, "M_inner": M,
-                          "operator_tile": pcg_loop_name(s, tile_rows) + f" (autotuned; us per PCG step {tile_us})",
+                          "operator_tile": pcg_loop_name(s, tile_rows) + (f" (autotuned; us per PCG step {tile_us})"
+                                                                          if args.tile is None else " (fixed)"),
                           "l2": "inputs (20 MB per frame of planes, 190 MB per PCG vector set) exceed the L2"},
                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                               "max": float(lat.max()), "first_frame": float(lat[0])},
