@@ -57,6 +57,9 @@ def parse():
                          "oracle (each solved from the GPU's state at the previous frame; minutes of host time)")
     ap.add_argument("--tile-cache", default=None,
                     help="batch workload: file of autotuned tile shapes to read and extend (default: none)")
+    ap.add_argument("--l2-window", action="store_true",
+                    help="video and stream workloads: the PCG launches mark the operator coefficients persisting "
+                         "in L2 (gid_set_l2_window)")
     ap.add_argument("--batch-form", default="worklist", choices=["worklist", "branch"],
                     help="batch workload: PCG steps as work-list launches over all videos of one K (default) or "
                          "one graph branch per video with autotuned tile shapes")
@@ -377,6 +380,8 @@ def run_gid(args, ws, rank, local):
     else:
         s.set_apply_tile(args.tile)
         tile_rows, tile_us = args.tile, "fixed by --tile"
+    if args.l2_window:
+        s.set_l2_window(True)
     for _ in range(args.warmup):
         flush.fill_(1.0)
         step()
@@ -652,7 +657,8 @@ def run_gid(args, ws, rank, local):
                           "M_inner": M, "l2": "flushed before each step (256 MB write, outside the events)",
                           "parallelism": f"replicas x{ws} (one video per GPU)",
                           "operator_tile": pcg_loop_name(s, tile_rows) +
-                          (f" (autotuned; us per PCG step {tile_us})" if args.tile is None else " (fixed)")},
+                          (f" (autotuned; us per PCG step {tile_us})" if args.tile is None else " (fixed)"),
+                          "l2_window": s.l2_window()},
                "gpu_launches": launches, "roofline": roof, "kernel_time_per_step": shares,
                "e2e": e2e, "cpu_baseline": cpu, "parity": parity, "clocks": clk, "final_energy": E,
                "learned_warm_start": learned, "editing": editing, "clustering": clustering,
@@ -948,6 +954,8 @@ def run_stream(args, ws, rank, local):
     else:
         s.set_apply_tile(args.tile)
         tile_rows, tile_us = args.tile, "fixed by --tile"
+    if args.l2_window:
+        s.set_l2_window(True)
 
     def frame(t):
         s.set_frame(rgb[t], lab[t])
@@ -988,6 +996,7 @@ def run_stream(args, ws, rank, local):
                           "frames": F, "N_outer": N, "M_inner": M,
                           "operator_tile": pcg_loop_name(s, tile_rows) + (f" (autotuned; us per PCG step {tile_us})"
                                                                           if args.tile is None else " (fixed)"),
+                          "l2_window": s.l2_window(),
                           "l2": "inputs (20 MB per frame of planes, 190 MB per PCG vector set) exceed the L2"},
                "latency_ms": {"p50": float(np.percentile(lat, 50)), "p99": float(np.percentile(lat, 99)),
                               "max": float(lat.max()), "first_frame": float(lat[0])},

@@ -270,6 +270,23 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 #define GID_PCG_FUSED 256
 int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
+/* on != 0: the PCG launches (operator, vector and fused steps) carry an L2
+ * access-policy window over the operator coefficient planes (NC planes, written
+ * once per Gauss-Newton step and read by every PCG step of it): accesses to them
+ * are marked persisting, up to the device's persisting-L2 limit, which the
+ * first context to turn this on raises to the planes' size (capped by the
+ * device maximum) for this process; the set-aside is released when the last
+ * context turns it off or is destroyed.  Only speed changes.  Synchronises and
+ * drops the context's cached graphs.  GID_ERR_INVALID_ARG if the device has no
+ * persisting L2 or the planes do not fit in its maximum set-aside whole (a
+ * partial window thrashes it: 1920 x 1080 K = 8 ran 52 % slower with one).
+ * gid_autotune times its chosen loop with and without the window and keeps the
+ * faster. */
+int gid_set_l2_window(gid_ctx* ctx, int on);
+
+/* 1 if the context's PCG launches carry the L2 window, 0 if not, -1 for NULL. */
+int gid_get_l2_window(const gid_ctx* ctx);
+
 /* The context's PCG loop (*rows as passed to gid_set_apply_tile) and the tile
  * geometry the resident loop has, or would have, on this frame: tile_w x
  * tile_h pixels, `blocks` tiles (0, 0, 0 if it does not fit).  Any pointer may
@@ -341,7 +358,9 @@ int gid_get_preconditioner(const gid_ctx* ctx);
  * persistent, resident, fused 2, 4, 8, 17; -1 if unavailable) to
  * us_out[GID_AUTOTUNE_TIMINGS]; either may be NULL.  The single-launch and
  * fused loops are timed as the difference of two Gauss-Newton steps (reps + 2
- * and 2 PCG steps), so that the linearisation does not count.  Needs gid_set_frame and a state; leaves the state X
+ * and 2 PCG steps), so that the linearisation does not count.  Where the
+ * operator coefficients fit in the persisting L2 set-aside, the chosen loop is
+ * then timed that way with and without gid_set_l2_window and the faster kept.  Needs gid_set_frame and a state; leaves the state X
  * unchanged (the PCG vectors are scratch until the next gid_run).  Call it
  * between runs.  Synchronises. */
 #define GID_AUTOTUNE_TIMINGS 10
@@ -394,7 +413,8 @@ int gid_batch_set_worklist(gid_batch* batch, int on);
 /* Choose every video's operator tile shape for the branch form: from the
  * cache file (lines "H W K rows") if it lists the video's shape, else by
  * gid_autotune(reps) on the video's current frame and state (the fastest
- * multi-kernel tile shape: batches do not run the single-launch loops), then
+ * multi-launch loop: a tile shape of the two-kernel loop or of the fused step;
+ * batches do not run the single-launch loops), then
  * append the new shapes to the file (cache_path may be NULL: no cache).  The
  * work-list form always uses 17-row tiles.  Needs frames and states.
  * Synchronises. */

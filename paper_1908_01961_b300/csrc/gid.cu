@@ -61,6 +61,8 @@ struct gid_ctx {
   bool persistent = false; // persistent PCG kernel selected (gid_set_apply_tile(0) / gid_autotune)
   bool resident = false;   // resident PCG kernel selected (gid_set_apply_tile(-1) / gid_autotune)
   bool fused = false;      // one-kernel PCG step selected (gid_set_apply_tile(rows | GID_PCG_FUSED))
+  bool l2_window = false;  // the PCG launches carry an L2 persistence window over the coefficients (gid_set_l2_window)
+  cudaAccessPolicyWindow l2win{};
   float* fbuf = nullptr;   // its odd-step z and M^-1 q buffers (2 x V planes, allocated on first use)
   ResTile res{};           // its tile geometry; res_blocks = 0 if the frame does not fit on chip
   CUtensorMap res_map;     // its coefficient stream: box [1 plane][TH + 1 rows][4 TX + 8 columns]
@@ -203,6 +205,8 @@ static Params params(const gid_ctx* c) {
 
 // How the PCG loop of a Gauss-Newton step runs: 0 one operator and one vector
 // kernel per step, 1 the persistent cooperative kernel, 2 the resident one.
+static void l2_release(gid_ctx* c);
+
 // 0: operator and vector kernel per PCG step; 1: persistent; 2: resident; 3: fused step
 static int pcg_kernel(const gid_ctx* c) {
   if (c->resident && c->res_blocks > 0) return 2;
@@ -291,11 +295,16 @@ struct Launch {
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = smem;
     cfg.stream = c->stream;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    if (c->l2_window) {
+      attr[1].id = cudaLaunchAttributeAccessPolicyWindow;
+      attr[1].val.accessPolicyWindow = c->l2win;
+      cfg.numAttrs = 2;
+    }
     cudaLaunchKernelEx(&cfg, kern, args...);
   }
   template <int TH>
@@ -746,6 +755,7 @@ extern "C" void gid_destroy(gid_ctx* c) {
   cudaFree(c->blk);
   cudaFree(c->zx);
   cudaFree(c->fbuf);
+  l2_release(c);
   cudaFree(c->xval);
   cudaFree(c->st_rgb);
   cudaFree(c->st_lab);
@@ -1409,6 +1419,61 @@ extern "C" int gid_get_pcg_layout(gid_ctx* c, int* rows, int* tile_w, int* tile_
   return GID_OK;
 }
 
+// ---------------------------------------------------------------- L2 persistence of the coefficients
+
+// Contexts of this process whose launches carry a window (the set-aside is
+// released when the last one turns it off or is destroyed).
+static int g_l2_users = 0;
+
+static void l2_release(gid_ctx* c) {
+  if (!c->l2_window) return;
+  c->l2_window = false;
+  if (--g_l2_users == 0) {
+    cudaCtxResetPersistingL2Cache();
+    cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, 0);
+    cudaGetLastError();
+  }
+}
+
+extern "C" int gid_get_l2_window(const gid_ctx* c) { return c ? (c->l2_window ? 1 : 0) : -1; }
+
+extern "C" int gid_set_l2_window(gid_ctx* c, int on) {
+  if (!c) return fail(c, GID_ERR_INVALID_ARG, "NULL ctx");
+  if ((on != 0) == c->l2_window) return GID_OK;
+  // the cached graphs hold launches with the other attribute set
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->gs) cudaStreamSynchronize(c->gs);
+  for (auto& gr : c->graphs) cudaGraphExecDestroy(gr.exec);
+  c->graphs.clear();
+  if (!on) {
+    l2_release(c);
+    return GID_OK;
+  }
+  int dev = 0, maxp = 0, maxw = 0;
+  GID_TRY_CUDA(c, cudaGetDevice(&dev));
+  GID_TRY_CUDA(c, cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev));
+  GID_TRY_CUDA(c, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev));
+  if (maxp <= 0 || maxw <= 0) return fail(c, GID_ERR_INVALID_ARG, "no persisting L2 on this device");
+  const size_t bytes = sizeof(float) * (size_t)coef_planes(c->K, c->w.n_spatial_pairs) * c->plane;
+  // a window the set-aside cannot hold whole thrashes it (measured slower than none)
+  if (bytes > (size_t)maxp || bytes > (size_t)maxw)
+    return fail(c, GID_ERR_INVALID_ARG, "the coefficient planes exceed the device's persisting L2");
+  const size_t win = bytes;
+  size_t cur = 0;
+  GID_TRY_CUDA(c, cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+  const size_t want = std::min(win, (size_t)maxp);
+  if (cur < want) GID_TRY_CUDA(c, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
+  GID_TRY_CUDA(c, cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
+  c->l2win.base_ptr = c->coef;
+  c->l2win.num_bytes = win;
+  c->l2win.hitRatio = std::min(1.0f, (float)cur / (float)win);
+  c->l2win.hitProp = cudaAccessPropertyPersisting;
+  c->l2win.missProp = cudaAccessPropertyStreaming;
+  c->l2_window = true;
+  g_l2_users++;
+  return GID_OK;
+}
+
 // ---------------------------------------------------------------- PCG history
 
 extern "C" int gid_set_pcg_history(gid_ctx* c, int on) {
@@ -1600,6 +1665,19 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
   c->apply_th = c->fused ? (choice & ~GID_PCG_FUSED) : th_tiled;
   c->persistent = choice == 0;
   c->resident = choice == GID_PCG_RESIDENT;
+  // the chosen loop with and without the L2 window over the coefficients (where
+  // they fit in the persisting set-aside): keep the faster
+  const bool had_window = c->l2_window;
+  if (gid_set_l2_window(c, 0) == GID_OK && gid_set_l2_window(c, 1) == GID_OK) {
+    float with = 0.f, without = 0.f;
+    if (int rc = time_loop(&with)) return rc;
+    gid_set_l2_window(c, 0);
+    if (int rc = time_loop(&without)) return rc;
+    if (with < without) gid_set_l2_window(c, 1);
+  } else {
+    c->err.clear();
+    gid_set_l2_window(c, had_window ? 1 : 0);
+  }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rows_out) *rows_out = choice;
@@ -2003,13 +2081,15 @@ extern "C" int gid_batch_autotune(gid_batch* b, const char* cache_path, int reps
     if (!found) {
       float us[GID_AUTOTUNE_TIMINGS];
       if (int rc = gid_autotune(c, reps, &rows, us)) return bfail(b, rc, gid_last_error(c));
-      if (rows <= 0) {  // batches run the multi-kernel PCG: keep its fastest tile shape
+      if (rows <= 0) {  // batches run multi-launch loops: keep the fastest of those
         const int cand[4] = {2, 4, 8, 17};
         int jb = 0;
-        for (int j = 1; j < 4; j++)
-          if (us[j] < us[jb]) jb = j;
-        rows = cand[jb];
+        for (int j = 1; j < GID_AUTOTUNE_TIMINGS; j++)
+          if ((j < 4 || j >= 6) && us[j] > 0.f && us[j] < us[jb]) jb = j;
+        rows = jb < 4 ? cand[jb] : (cand[jb - 6] | GID_PCG_FUSED);
       }
+      // the videos of a batch run at once: no context holds an L2 set-aside for itself
+      gid_set_l2_window(c, 0);
       cache.push_back({c->H, c->W, c->K, rows});
       dirty = true;
     }

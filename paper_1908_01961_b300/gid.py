@@ -20,6 +20,7 @@ PRECOND_JACOBI, PRECOND_BLOCK = 0, 1
 RESIDENT = -1  # gid_set_apply_tile: the resident PCG loop (GID_PCG_RESIDENT)
 FUSED = 256    # gid_set_apply_tile(rows | FUSED): one kernel per PCG step (GID_PCG_FUSED)
 AUTOTUNE_LOOPS = (2, 4, 8, 17, 0, RESIDENT, 2 | FUSED, 4 | FUSED, 8 | FUSED, 17 | FUSED)
+ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_STATE = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_NUMERIC = -5, -6
 ENERGY_TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness",
                 "non_neg")
@@ -37,7 +38,7 @@ EXPORTS = (
     "gid_set_state", "gid_energy", "gid_solve_frame_host", "gid_stage_precompute", "gid_stage_linearize",
     "gid_stage_apply", "gid_stage_pcg", "gid_stage_dense_normal", "gid_launch_count", "gid_profile",
     "gid_profile_read", "gid_new_sequence", "gid_dense_refine_noalloc", "gid_set_apply_tile", "gid_get_pcg_layout",
-    "gid_autotune",
+    "gid_autotune", "gid_set_l2_window", "gid_get_l2_window",
     "gid_set_preconditioner", "gid_get_preconditioner", "gid_debug_inject", "gid_pcg_history",
     "gid_set_pcg_history",
     "gid_set_graphs", "gid_batch_create", "gid_batch_destroy", "gid_batch_last_error", "gid_batch_ctx",
@@ -131,6 +132,8 @@ def load():
     L.gid_batch_new_sequence.argtypes = [P]
     L.gid_batch_run.argtypes = [P, I, I]
     L.gid_batch_autotune.argtypes = [P, ctypes.c_char_p, I]
+    L.gid_set_l2_window.argtypes = [P, I]
+    L.gid_get_l2_window.argtypes = [P]
     L.gid_batch_set_worklist.argtypes = [P, I]
     L.gid_net_create.argtypes = [I, ctypes.POINTER(I), ctypes.c_uint64, P, ctypes.POINTER(P)]
     L.gid_net_destroy.argtypes = [P]
@@ -512,6 +515,13 @@ class Solver:
         us = (ctypes.c_float * len(AUTOTUNE_LOOPS))()
         self._chk(self.lib.gid_autotune(self.h, reps, ctypes.byref(rows), us))
         return rows.value, dict(zip(AUTOTUNE_LOOPS, us[:]))
+
+    def set_l2_window(self, on: bool):
+        """Mark the operator coefficients persisting in L2 for the PCG launches (gid_set_l2_window)."""
+        self._chk(self.lib.gid_set_l2_window(self.h, 1 if on else 0))
+
+    def l2_window(self) -> bool:
+        return self.lib.gid_get_l2_window(self.h) == 1
 
     def pcg_layout(self):
         """(rows of the current PCG loop, (tile_w, tile_h, blocks) of the resident loop on this
