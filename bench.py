@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip the learned warm-start comparison")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the editing, clustering, correction and preconditioner measurements (profiling runs)")
-    ap.add_argument("--tile", type=int, default=None, choices=[-1, 0, 2, 4, 8, 17, 258, 260, 264, 273],
+    ap.add_argument("--tile", type=int, default=None, choices=[-1, 0, 2, 4, 8, 16, 17, 258, 260, 264, 273],
                     help="PCG loop instead of autotuning: operator tile rows, 0 = persistent kernel, "
                          "-1 = resident kernel, rows + 256 = fused step; for profiling")
     ap.add_argument("--parity", action="store_true",

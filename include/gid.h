@@ -238,8 +238,9 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 /* ---- operator tile shape ---- */
 
 /* How the PCG loop of each Gauss-Newton step (Sec. 6.1) runs.  rows = 2, 4
- * (default), 8 or 17: one operator kernel and one vector kernel per PCG step,
- * operator tiles of 128 x rows pixels (17 runs one 544-thread block per SM).
+ * (default), 8, 16 or 17: one operator kernel and one vector kernel per PCG
+ * step, operator tiles of 128 x rows pixels (17 runs one 544-thread block per
+ * SM at up to 96 registers a thread, 16 one 512-thread block at up to 128).
  * rows = 0: all PCG steps of a Gauss-Newton step in one cooperative launch
  * (one block per SM streaming every vector, operator and vector phases
  * separated by grid barriers whose waits are bounded; a barrier that gives up
@@ -351,11 +352,11 @@ int gid_set_preconditioner(gid_ctx* ctx, int kind);
 /* The context's preconditioner (GID_PRECOND_*), -1 for a NULL ctx. */
 int gid_get_preconditioner(const gid_ctx* ctx);
 
-/* Time reps PCG steps with each of the ten ways above on the current frame
+/* Time reps PCG steps with each of the eleven ways above on the current frame
  * and state (CUDA events on the context stream) and keep the fastest.  Writes
  * the chosen rows (0 = persistent, GID_PCG_RESIDENT, rows | GID_PCG_FUSED) to
- * *rows_out and the ten timings (us per PCG step; shapes 2, 4, 8, 17,
- * persistent, resident, fused 2, 4, 8, 17; -1 if unavailable) to
+ * *rows_out and the eleven timings (us per PCG step; shapes 2, 4, 8, 17,
+ * persistent, resident, fused 2, 4, 8, 17, shape 16; -1 if unavailable) to
  * us_out[GID_AUTOTUNE_TIMINGS]; either may be NULL.  The single-launch and
  * fused loops are timed as the difference of two Gauss-Newton steps (reps + 2
  * and 2 PCG steps), so that the linearisation does not count.  Where the
@@ -363,7 +364,7 @@ int gid_get_preconditioner(const gid_ctx* ctx);
  * then timed that way with and without gid_set_l2_window and the faster kept.  Needs gid_set_frame and a state; leaves the state X
  * unchanged (the PCG vectors are scratch until the next gid_run).  Call it
  * between runs.  Synchronises. */
-#define GID_AUTOTUNE_TIMINGS 10
+#define GID_AUTOTUNE_TIMINGS 11
 int gid_autotune(gid_ctx* ctx, int reps, int* rows_out, float* us_out);
 
 /* ---- batches of videos (many videos of uneven size, one graph per step) ---- */

@@ -358,6 +358,7 @@ struct Launch {
     cudaFuncSetAttribute(k_apply<K, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 2>));
     cudaFuncSetAttribute(k_apply<K, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 4>));
     cudaFuncSetAttribute(k_apply<K, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 8>));
+    cudaFuncSetAttribute(k_apply<K, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 16>));
     cudaFuncSetAttribute(k_apply<K, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(ApplyTile<K, 17>));
     cudaFuncSetAttribute(k_apply_multi<K, 17>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)sizeof(ApplyTile<K, 17>));
@@ -366,6 +367,7 @@ struct Launch {
     switch (c->apply_th) {
       case 2: apply_th<2>(c, mode, first, it, pin, pout, qout); break;
       case 4: apply_th<4>(c, mode, first, it, pin, pout, qout); break;
+      case 16: apply_th<16>(c, mode, first, it, pin, pout, qout); break;
       case 17: apply_th<17>(c, mode, first, it, pin, pout, qout); break;
       default: apply_th<8>(c, mode, first, it, pin, pout, qout); break;
     }
@@ -1396,9 +1398,9 @@ extern "C" int gid_set_apply_tile(gid_ctx* c, int rows) {
   }
   const bool fused = rows > 0 && (rows & GID_PCG_FUSED);
   if (fused) rows &= ~GID_PCG_FUSED;
-  if (rows != 2 && rows != 4 && rows != 8 && rows != 17)
+  if ((rows != 2 && rows != 4 && rows != 8 && rows != 16 && rows != 17) || (fused && rows == 16))
     return fail(c, GID_ERR_INVALID_ARG,
-                "tile rows must be -1 (resident), 0 (persistent), 2, 4, 8 or 17 (optionally | GID_PCG_FUSED)");
+                "tile rows must be -1 (resident), 0 (persistent), 2, 4, 8, 16 or 17 (2, 4, 8 or 17 | GID_PCG_FUSED)");
   if (fused)
     if (int rc = fused_prepare(c)) return rc;
   c->apply_th = rows;
@@ -1567,14 +1569,15 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
   cudaEvent_t e0, e1;
   GID_TRY_CUDA(c, cudaEventCreate(&e0));
   GID_TRY_CUDA(c, cudaEventCreate(&e1));
-  const int cand[4] = {2, 4, 8, 17};
+  // the two-kernel loop's tile shapes and their slots in us_out (16 rows came last)
+  const int cand[4] = {2, 4, 8, 17}, tiled[5] = {2, 4, 8, 17, 16}, slot[5] = {0, 1, 2, 3, 10};
   float best = 1e30f;
   int best_th = c->apply_th;
   c->persistent = false;
   c->resident = false;
   c->fused = false;
-  for (int i = 0; i < 4; i++) {
-    c->apply_th = cand[i];
+  for (int i = 0; i < 5; i++) {
+    c->apply_th = tiled[i];
     int it = 0;
     auto pair = [&](int first) {
       ++it;
@@ -1593,10 +1596,10 @@ extern "C" int gid_autotune(gid_ctx* c, int reps, int* rows_out, float* us_out) 
     float ms = 0.f;
     GID_TRY_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
     const float us = 1000.f * ms / reps;
-    if (us_out) us_out[i] = us;
+    if (us_out) us_out[slot[i]] = us;
     if (us < best) {
       best = us;
-      best_th = cand[i];
+      best_th = tiled[i];
     }
   }
   c->apply_th = best_th;
@@ -2086,7 +2089,7 @@ extern "C" int gid_batch_autotune(gid_batch* b, const char* cache_path, int reps
         int jb = 0;
         for (int j = 1; j < GID_AUTOTUNE_TIMINGS; j++)
           if ((j < 4 || j >= 6) && us[j] > 0.f && us[j] < us[jb]) jb = j;
-        rows = jb < 4 ? cand[jb] : (cand[jb - 6] | GID_PCG_FUSED);
+        rows = jb < 4 ? cand[jb] : (jb == 10 ? 16 : (cand[jb - 6] | GID_PCG_FUSED));
       }
       // the videos of a batch run at once: no context holds an L2 set-aside for itself
       gid_set_l2_window(c, 0);

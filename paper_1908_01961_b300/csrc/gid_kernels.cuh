@@ -790,6 +790,12 @@ struct ApplyShape<2> {
 // 17 rows, one 544-thread block per SM: a 640 x 480 frame is 145 such tiles,
 // one wave on 148 SMs.  17 warps put 5 warps on one SM sub-partition (16 K
 // registers), hence at most 96 registers per thread.
+// 16 rows, one 512-thread block per SM at up to 128 registers (16 warps: 4 per
+// sub-partition); for frames whose 17-row tiles spill at 96 registers (K >= 7).
+template <>
+struct ApplyShape<16> {
+  static constexpr int MINB = 1, MAXREG = 128;
+};
 template <>
 struct ApplyShape<17> {
   static constexpr int MINB = 1, MAXREG = 96;
@@ -1075,7 +1081,7 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
       pq += dot4(p, q);
     };
     const int cx = VHX + QW * threadIdx.x, ry = threadIdx.y + AHR, ty = threadIdx.y + 1;
-    op_apply4<K, TH >= 17>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
+    op_apply4<K, TH >= 16>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
                            VRW, finish);
   }
   return pq;
@@ -2389,7 +2395,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
       zq += dot4(s, q);
       qmq += dot4(q, mq);
     };
-    op_apply4<K, TH >= 17>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
+    op_apply4<K, TH >= 16>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
                            VRW, finish);
   }
   double part[RES_NV];

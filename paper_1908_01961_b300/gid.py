@@ -19,7 +19,7 @@ GID_OK = 0
 PRECOND_JACOBI, PRECOND_BLOCK = 0, 1
 RESIDENT = -1  # gid_set_apply_tile: the resident PCG loop (GID_PCG_RESIDENT)
 FUSED = 256    # gid_set_apply_tile(rows | FUSED): one kernel per PCG step (GID_PCG_FUSED)
-AUTOTUNE_LOOPS = (2, 4, 8, 17, 0, RESIDENT, 2 | FUSED, 4 | FUSED, 8 | FUSED, 17 | FUSED)
+AUTOTUNE_LOOPS = (2, 4, 8, 17, 0, RESIDENT, 2 | FUSED, 4 | FUSED, 8 | FUSED, 17 | FUSED, 16)
 ERR_INVALID_ARG, ERR_CUDA, ERR_OOM, ERR_STATE = -1, -2, -3, -4
 ERR_TIMEOUT, ERR_NUMERIC = -5, -6
 ENERGY_TERMS = ("data", "clustering", "r_sparsity", "r_consistency", "monochrome", "i_sparsity", "smoothness",

@@ -222,7 +222,7 @@ def test_graph_replay_matches_direct_launches():
     assert out[0][2] == out[1][2]
 
 
-@pytest.mark.parametrize("rows", [2, 4, 8, 17])
+@pytest.mark.parametrize("rows", [2, 4, 8, 16, 17])
 def test_operator_tile_shapes_agree(rows):
     """Every operator tile shape computes the same J^T J p (up to FP32 rounding order)."""
     case = Case(**CASES["70x41_K6"], seed=3)
@@ -353,3 +353,22 @@ def test_recombine_full_size_640x480_K6():
     out = s.recombine(bn, g, torch.from_numpy(mask).cuda())
     ref = O.recombine(X, b, bn.astype(np.float64), g.astype(np.float64), mask)
     close(out.cpu().numpy(), ref, 1e-5, "recombined image")
+
+
+@pytest.mark.parametrize("rows", [8, 16, 17])
+def test_k8_pcg_delta_each_tile_shape(rows):
+    """K = 8 (the 1080p stream's K), 10 PCG steps from a perturbed state with
+    the unrolled 8-row, and the rolled 16- and 17-row tiles (128 and 96
+    registers): delta within 1e-4 of its max against the oracle; ragged tiles in
+    both directions."""
+    case = Case(H=57, W=150, K=8, n_cells=10, seed=5)
+    s = case.solver()
+    s.set_apply_tile(rows)
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    pb = case.oracle_problem()
+    X = random_state(case, pb, 2)
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    delta = s.stage_pcg(10)
+    ref, _ = pb.pcg(X, 10)
+    close(delta.cpu().numpy(), ref, tol=1e-4, what=f"PCG delta K=8, {rows} rows")
