@@ -791,7 +791,9 @@ struct ApplyShape<2> {
 // one wave on 148 SMs.  17 warps put 5 warps on one SM sub-partition (16 K
 // registers), hence at most 96 registers per thread.
 // 16 rows, one 512-thread block per SM at up to 128 registers (16 warps: 4 per
-// sub-partition); for frames whose 17-row tiles spill at 96 registers (K >= 7).
+// sub-partition): for frames large enough that the 17-row tile's single wave
+// does not matter (1920 x 1080, the batch's work list), where it also avoids
+// the 96-register spills of K >= 7.
 template <>
 struct ApplyShape<16> {
   static constexpr int MINB = 1, MAXREG = 128;
