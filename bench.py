@@ -820,7 +820,7 @@ def run_batch(args, ws, rank, local):
 
     step()
     if args.batch_form == "branch":
-        batch.autotune(args.tile_cache, reps=5)   # the work-list form always uses 128 x 16 tiles
+        batch.autotune(args.tile_cache, reps=5)   # the work-list form always uses 128 x 4 tiles
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         flush.fill_(1.0)
@@ -858,7 +858,7 @@ def run_batch(args, ws, rank, local):
                "config": {"workload": f"batch of 24 videos x {BATCH_FRAMES} frames, one CUDA graph launch per "
                                       "frame-step for all videos",
                           "pcg_launches": ("one operator and one vector launch per K and PCG step over all videos "
-                                           "of that K (128 x 16 tiles)" if args.batch_form == "worklist" else
+                                           "of that K (128 x 4 tiles)" if args.batch_form == "worklist" else
                                            "one graph branch per video, tile shapes autotuned per frame size"),
                           "megapixels_per_frame_step": px / BATCH_FRAMES / 1e6,
                           "l2": "flushed before each step (256 MB write, outside the events)"},

@@ -395,7 +395,7 @@ int gid_batch_new_sequence(gid_batch* batch);
  * video uses the Jacobi preconditioner): per Gauss-Newton step each video
  * linearises on its own stream, then each of the M PCG steps (Sec. 6.1) is one
  * operator launch and one vector launch per distinct K covering the tiles and
- * planes of every video with that K (operator tiles of 128 x 16 pixels), then
+ * planes of every video with that K (operator tiles of 128 x 4 pixels), then
  * each video takes its base-colour step on its own stream.  Branch form
  * (gid_batch_set_worklist(batch, 0), or any video with the block
  * preconditioner): each video's own multi-kernel launch sequence (tile rows
@@ -417,7 +417,7 @@ int gid_batch_set_worklist(gid_batch* batch, int on);
  * multi-launch loop: a tile shape of the two-kernel loop or of the fused step;
  * batches do not run the single-launch loops), then
  * append the new shapes to the file (cache_path may be NULL: no cache).  The
- * work-list form always uses 16-row tiles.  Needs frames and states.
+ * work-list form always uses 4-row tiles.  Needs frames and states.
  * Synchronises. */
 int gid_batch_autotune(gid_batch* batch, const char* cache_path, int reps);
 

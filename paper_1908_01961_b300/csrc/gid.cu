@@ -279,10 +279,12 @@ static const gid_ctx::Maps* tile_maps(gid_ctx* c, const float* base, int th) {
 
 // ---------------------------------------------------------------- K dispatch
 
-// Operator tile rows of the work-list launches: 16 (four warps per SM
-// sub-partition, 128 registers) measured 4 % faster over the 24-video batch
-// than 17, whose one-wave advantage at 640 x 480 does not apply there.
-constexpr int WL_TH = 16;
+// Operator tile rows of the work-list launches: 4 (four 128-thread blocks per
+// SM, so one block's staging overlaps another's arithmetic).  Over the 24-video
+// batch (many tiles, HBM-bound) 128 x 4 tiles ran at 46.3 Mpx/s, 128 x 8 at 45.7,
+// 128 x 16 at 43.3 and 128 x 17 (the single 640 x 480 frame's one-wave tile) at
+// 41.4.
+constexpr int WL_TH = 4;
 
 template <int K>
 struct Launch {

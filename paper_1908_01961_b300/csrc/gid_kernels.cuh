@@ -812,11 +812,13 @@ struct ApplyShape<17> {
 // reflectance channels, 1 row and 4 columns for the layers, zero outside the
 // frame).  finish(v, s_v, (A s)_v) is called once per plane v (reflectance
 // channels first) with the four pixels' values; lanes past the frame's right
-// edge of A s are zero.  ROLL: the layer loop is not unrolled (register budget).
+// edge of A s are zero.  The layer loop is not unrolled: unrolled, the 2-, 4- and
+// 8-row tiles spilled at 128 registers (416 bytes at K = 8) and ran 4-8 %
+// slower on frames of many tiles.
 // SHFL: the left neighbour's right-edge weights come from lane - 1 of the warp
 // where left_lane says that lane holds the chunk to the left (every lane of the
 // warp must then make the call); elsewhere they are loaded.
-template <int K, bool ROLL, bool SHFL = false, class FIN>
+template <int K, bool SHFL = false, class FIN>
 __device__ __forceinline__ void op_apply4(const Params& P, const ColorTable<K>& ct, int x, int y,
                                           const float* sr, int SRC, int SRR, const float* st, int STC, int STR,
                                           FIN finish, bool left_lane = false) {
@@ -891,7 +893,7 @@ __device__ __forceinline__ void op_apply4(const Params& P, const ColorTable<K>& 
     for (int c = 0; c < 3; c++) Mc[c] = mul4(wm, Mc[c]);
   }
   // layers: data and monochrome back-projections, diagonal IRLS weights, smoothness
-#pragma unroll(ROLL ? 1 : K + 1)
+#pragma unroll 1
   for (int k = 0; k <= K; k++) {
     const float* row = st + k * STC;
     const F4 pk = lds4(row);
@@ -1083,7 +1085,7 @@ __device__ __forceinline__ float apply_tile(const Params& P, ApplyTile<K, TH>& t
       pq += dot4(p, q);
     };
     const int cx = VHX + QW * threadIdx.x, ry = threadIdx.y + AHR, ty = threadIdx.y + 1;
-    op_apply4<K, TH >= 16>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
+    op_apply4<K>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
                            VRW, finish);
   }
   return pq;
@@ -2397,7 +2399,7 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
       zq += dot4(s, q);
       qmq += dot4(q, mq);
     };
-    op_apply4<K, TH >= 16>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
+    op_apply4<K>(P, ct, x, y, &t.pr[0][ry][cx], (TH + 2 * AHR) * VRW, VRW, &t.pt[0][ty][cx], (TH + 2) * VRW,
                            VRW, finish);
   }
   double part[RES_NV];
