@@ -237,10 +237,12 @@ int gid_stage_dense_normal(gid_ctx* ctx, double* A_host, double* g_host);
 
 /* ---- operator tile shape ---- */
 
-/* How the PCG loop of each Gauss-Newton step (Sec. 6.1) runs.  rows = 2, 4
- * (default), 8, 16 or 17: one operator kernel and one vector kernel per PCG
- * step, operator tiles of 128 x rows pixels (17 runs one 544-thread block per
- * SM at up to 96 registers a thread, 16 one 512-thread block at up to 128).
+/* How the PCG loop of each Gauss-Newton step (Sec. 6.1) runs.  rows = 2, 4, 8,
+ * 16 or 17: one operator kernel and one vector kernel per PCG step, operator
+ * tiles of 128 x rows pixels (17 runs one 544-thread block per SM at up to 96
+ * registers a thread, 16 one 512-thread block at up to 128).  A new context
+ * starts with 17 if the frame's 128 x 17 tiles fit in one wave (at most one
+ * per SM), else 4.
  * rows = 0: all PCG steps of a Gauss-Newton step in one cooperative launch
  * (one block per SM streaming every vector, operator and vector phases
  * separated by grid barriers whose waits are bounded; a barrier that gives up

@@ -54,7 +54,7 @@ struct gid_ctx {
   bool has_colors = false, has_frame = false, initialised = false, temporal_active = false;
   int frames_solved = 0;
   long long launches = 0;  // kernels launched by this context
-  int apply_th = 4;        // rows per operator tile (gid_set_apply_tile / gid_autotune)
+  int apply_th = 4;        // rows per operator tile (set by frame size at creation; gid_set_apply_tile / gid_autotune)
   int pcg_blocks = 0;      // > 0: run the PCG loop as one cooperative launch of this many blocks
   int upd_cap = 148 * 4;   // vector-step blocks resident at once (SMs x blocks per SM)
   int dense_cap = 148;     // base-colour-step blocks resident at once
@@ -671,6 +671,16 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
     default: c->dense_cap = Launch<10>::dense_capacity(c); break;
   }
   cudaGetLastError();
+  {
+    // default operator tile (before any gid_autotune): 17 rows where the frame's
+    // 128 x 17 tiles fit in one wave of one block per SM, else 4 rows (four
+    // blocks per SM; many tiles, where small tiles overlap best)
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const long n17 = (long)((W + VTW - 1) / VTW) * ((H + 16) / 17);
+    c->apply_th = sms > 0 && n17 <= sms ? 17 : 4;
+  }
   const long nb = std::max((long)pix_grid(c).x * pix_grid(c).y, (long)((W + VTW - 1) / VTW) * ((H + 1) / 2));
   const long nb_update = (c->plane / 4 + 255) / 256 * c->V;
   const long npart = std::max({nb * 8, nb_update, (long)dense_blocks(c) * 3 * (GID_MAX_K * (GID_MAX_K + 1) / 2 + GID_MAX_K)});
