@@ -60,9 +60,10 @@ def parse():
     ap.add_argument("--l2-window", action="store_true",
                     help="video and stream workloads: the PCG launches mark the operator coefficients persisting "
                          "in L2 (gid_set_l2_window)")
-    ap.add_argument("--batch-form", default="worklist", choices=["worklist", "branch"],
-                    help="batch workload: PCG steps as work-list launches over all videos of one K (default) or "
-                         "one graph branch per video with autotuned tile shapes")
+    ap.add_argument("--batch-form", default="worklist", choices=["worklist", "persistent", "branch"],
+                    help="batch workload: PCG steps as work-list launches over all videos of one K (default), the "
+                         "work list as one cooperative launch per K and Gauss-Newton step, or one graph branch per "
+                         "video with autotuned tile shapes")
     ap.add_argument("--workload", default="video", choices=["video", "batch", "stream"],
                     help="video: the 640x480 K=6 video (default); batch: 24 uneven videos in one graph per step")
     return ap.parse_args()
@@ -807,7 +808,7 @@ def run_batch(args, ws, rank, local):
         rgb.append([torch.from_numpy(x).to(dev) for x in frames_I])
         lab.append([torch.from_numpy(x).to(dev) for x in frames_lab])
     batch = gid.Batch(shapes, weights)
-    batch.set_worklist(args.batch_form == "worklist")
+    batch.set_worklist(args.batch_form != "branch", args.batch_form == "persistent")
     for v, b0 in zip(batch.videos, vids):
         v.set_base_colors(b0)
 
@@ -857,9 +858,12 @@ def run_batch(args, ws, rank, local):
                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
                "config": {"workload": f"batch of 24 videos x {BATCH_FRAMES} frames, one CUDA graph launch per "
                                       "frame-step for all videos",
-                          "pcg_launches": ("one operator and one vector launch per K and PCG step over all videos "
-                                           "of that K (128 x 4 tiles)" if args.batch_form == "worklist" else
-                                           "one graph branch per video, tile shapes autotuned per frame size"),
+                          "pcg_launches": {"worklist": "one operator and one vector launch per K and PCG step "
+                                                       "over all videos of that K (128 x 4 tiles)",
+                                           "persistent": "one cooperative launch per K and Gauss-Newton step over "
+                                                         "all videos of that K (128 x 4 tiles, grid barriers)",
+                                           "branch": "one graph branch per video, tile shapes autotuned per frame "
+                                                     "size"}[args.batch_form],
                           "megapixels_per_frame_step": px / BATCH_FRAMES / 1e6,
                           "l2": "flushed before each step (256 MB write, outside the events)"},
                "pixels_per_s": ws * args.steps * px / (total_ms / 1000.0), "gpu_launches": launches,

@@ -408,9 +408,12 @@ int gid_batch_new_sequence(gid_batch* batch);
  * Asynchronous. */
 int gid_batch_run(gid_batch* batch, int n_outer, int m_inner);
 
-/* on != 0: the work-list form of gid_batch_run (default); 0: the branch form.
- * Takes effect at the next gid_batch_run (graphs of both forms are kept).
- * GID_ERR_INVALID_ARG for a NULL batch. */
+/* on = 1: the work-list form of gid_batch_run (default); 2: the work list as
+ * one cooperative launch per K group and Gauss-Newton step (all M PCG steps,
+ * operator and vector phases separated by bounded grid barriers; the launch
+ * fails with GID_ERR_CUDA where the device cannot co-schedule it); 0: the
+ * branch form.  Takes effect at the next gid_batch_run (graphs of every form
+ * are kept).  GID_ERR_INVALID_ARG for a NULL batch. */
 int gid_batch_set_worklist(gid_batch* batch, int on);
 
 /* Choose every video's operator tile shape for the branch form: from the

@@ -474,6 +474,37 @@ struct Launch {
     c->res_smem = smem;
     c->res_blocks = nb;
   }
+  // The persistent work list of a batch group with this K: co-resident blocks
+  // per SM (0 if it cannot run cooperatively), and its launch.
+  static int pcg_multi_capacity() {
+    int dev = 0, sms = 0, coop = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev);
+    if (!coop ||
+        cudaFuncSetAttribute(k_pcg_multi<K, WL_TH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)sizeof(ApplyTile<K, WL_TH>)) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pcg_multi<K, WL_TH>, BX * WL_TH,
+                                                      sizeof(ApplyTile<K, WL_TH>)) != cudaSuccess) {
+      cudaGetLastError();
+      return 0;
+    }
+    return sms * per_sm;
+  }
+  static cudaError_t pcg_multi(cudaStream_t s, const MultiVideo* vids, int nv, const CUtensorMap* maps, int tiles,
+                               int upd, int m_inner, DevScalars* bar, int blocks) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(BX, WL_TH);
+    cfg.dynamicSmemBytes = sizeof(ApplyTile<K, WL_TH>);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_pcg_multi<K, WL_TH>, vids, nv, maps, tiles, upd, m_inner, bar);
+  }
   // Work-list PCG steps of a batch's videos with this K (operator tiles of 128 x WL_TH).
   static void apply_multi(cudaStream_t s, const MultiVideo* vids, int nv, const CUtensorMap* maps, int first, int it,
                           int blocks) {
@@ -1722,6 +1753,7 @@ struct gid_batch {
   };
   std::vector<Graph> graphs;
   bool worklist = true;  // PCG steps as work-list launches per K (gid_batch_set_worklist)
+  bool persistent_wl = false;  // ... as one cooperative launch per K and Gauss-Newton step
   std::string err;
 };
 
@@ -1849,6 +1881,7 @@ struct WorkGroup {
   MultiVideo* dv = nullptr;
   CUtensorMap* dm = nullptr;
   int tiles = 0, upd = 0;
+  int coop = 0;  // co-resident blocks of the persistent form (0: not available)
 };
 
 // The device tables of the work-list launches (made before the capture: the
@@ -1892,6 +1925,21 @@ static bool build_worklist(gid_batch* b, std::vector<WorkGroup>& groups, std::ve
       mv.upd0 = gr.upd;
       gr.tiles += mv.ntiles;
       gr.upd += mv.nupd;
+    }
+    if (b->persistent_wl) {
+      switch (gr.K) {
+        case 1: gr.coop = Launch<1>::pcg_multi_capacity(); break;
+        case 2: gr.coop = Launch<2>::pcg_multi_capacity(); break;
+        case 3: gr.coop = Launch<3>::pcg_multi_capacity(); break;
+        case 4: gr.coop = Launch<4>::pcg_multi_capacity(); break;
+        case 5: gr.coop = Launch<5>::pcg_multi_capacity(); break;
+        case 6: gr.coop = Launch<6>::pcg_multi_capacity(); break;
+        case 7: gr.coop = Launch<7>::pcg_multi_capacity(); break;
+        case 8: gr.coop = Launch<8>::pcg_multi_capacity(); break;
+        case 9: gr.coop = Launch<9>::pcg_multi_capacity(); break;
+        default: gr.coop = Launch<10>::pcg_multi_capacity(); break;
+      }
+      if (gr.coop <= 0) return false;
     }
     if (cudaMalloc(&gr.dv, sizeof(MultiVideo) * nv) != cudaSuccess) return false;
     tables.push_back(gr.dv);
@@ -1964,7 +2012,28 @@ static long long enqueue_worklist(gid_batch* b, std::vector<WorkGroup>& groups, 
       return 1;
     });
     if (!ok) return -1;
-    for (int m = 1; m <= m_inner; m++) {
+    if (b->persistent_wl) {
+      for (auto& gr : groups) {
+        DevScalars* bar = b->ctx[gr.vid[0]]->sc;
+        const int nv = (int)gr.vid.size();
+        cudaError_t e = cudaSuccess;
+        switch (gr.K) {
+          case 1: e = Launch<1>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 2: e = Launch<2>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 3: e = Launch<3>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 4: e = Launch<4>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 5: e = Launch<5>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 6: e = Launch<6>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 7: e = Launch<7>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 8: e = Launch<8>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          case 9: e = Launch<9>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+          default: e = Launch<10>::pcg_multi(b->bs, gr.dv, nv, gr.dm, gr.tiles, gr.upd, m_inner, bar, gr.coop); break;
+        }
+        if (e != cudaSuccess) return -1;
+        kernels++;
+      }
+    }
+    for (int m = 1; m <= m_inner && !b->persistent_wl; m++) {
       for (auto& gr : groups) {
         enqueue_apply_multi(b, gr, m);
         kernels++;
@@ -1987,6 +2056,7 @@ static long long enqueue_worklist(gid_batch* b, std::vector<WorkGroup>& groups, 
 extern "C" int gid_batch_set_worklist(gid_batch* b, int on) {
   if (!b) return bfail(b, GID_ERR_INVALID_ARG, "NULL batch");
   b->worklist = on != 0;
+  b->persistent_wl = on == 2;
   return GID_OK;
 }
 
@@ -1997,7 +2067,7 @@ extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
   // the work-list form needs Jacobi PCG in every video
   bool wl = b->worklist;
   for (int i = 0; i < b->n; i++) wl = wl && b->ctx[i]->precond == GID_PRECOND_JACOBI;
-  std::string key = std::to_string(n_outer) + "," + std::to_string(m_inner) + (wl ? ",w" : ",b");
+  std::string key = std::to_string(n_outer) + "," + std::to_string(m_inner) + (wl ? (b->persistent_wl ? ",p" : ",w") : ",b");
   std::vector<int> refine(b->n);
   for (int i = 0; i < b->n; i++) {
     gid_ctx* c = b->ctx[i];

@@ -1237,13 +1237,15 @@ struct MultiVideo {
   int tile0, upd0; // the video's first block in the operator / vector launch
 };
 
-// The video (index into vids) that owns block b of a launch, by first[v] =
-// tile0 or upd0, copied into shared memory; returns the block's index within
-// its video.  All threads call.
+// The video (index into vids) that owns block b of a launch (default: this
+// block), by first[v] = tile0 or upd0, copied into shared memory; returns the
+// block's index within its video.  All threads call.
 template <bool UPD>
-__device__ __forceinline__ int multi_video(const MultiVideo* __restrict__ vids, int nv, MultiVideo& mv, int& v) {
+__device__ __forceinline__ int multi_video(const MultiVideo* __restrict__ vids, int nv, MultiVideo& mv, int& v,
+                                           int b = -1) {
   __shared__ int vsel;
-  const int tid = tid_flat(), nth = blockDim.x * blockDim.y, b = blockIdx.x;
+  const int tid = tid_flat(), nth = blockDim.x * blockDim.y;
+  if (b < 0) b = blockIdx.x;
   if (tid == 0) {
     int s = 0;
     while (s + 1 < nv && (UPD ? vids[s + 1].upd0 : vids[s + 1].tile0) <= b) s++;
@@ -1674,6 +1676,69 @@ __global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
     rho_old = rho;
     rho = block_total(part_share(part_rz, nb));
     if (b == 0 && tid == 0 && m < PCG_HIST) P.sc->rho_hist[m] = rho;
+  }
+}
+
+// The work list of a batch group (videos of one K) as one cooperative launch
+// per Gauss-Newton step: all M PCG steps, each an operator phase over the
+// group's tiles and a vector phase over its vector blocks of nupd x 256 items
+// (both grid-strided over the list, so any number of co-resident blocks covers
+// them), separated by bounded grid barriers on the first video's arrival
+// counters (cleared by its k_linearize).  Each tile and vector block keeps its
+// video's scalars and partial slots exactly as k_apply_multi / k_update_multi
+// do.
+template <int K, int TH>
+__global__ void __launch_bounds__(BX * TH) __maxnreg__(ApplyShape<TH>::MAXREG)
+    k_pcg_multi(const MultiVideo* __restrict__ vids, int nv, const CUtensorMap* __restrict__ maps, int ntiles,
+                int nupd, int m_inner, DevScalars* bar) {
+  extern __shared__ __align__(128) float4 apply_smem[];
+  ApplyTile<K, TH>& t = *reinterpret_cast<ApplyTile<K, TH>*>(apply_smem);
+  __shared__ ColorTable<K> ct;
+  __shared__ MultiVideo mv;
+  const int nb = gridDim.x, b = blockIdx.x, tid = tid_flat(), nth = blockDim.x * blockDim.y;
+  for (int m = 1; m <= m_inner; m++) {
+    const int first = m == 1;
+    for (int tile = b; tile < ntiles; tile += nb) {
+      int v;
+      const int local = multi_video<false>(vids, nv, mv, v, tile);
+      const Params& P = mv.P;
+      load_colors<K>(ct, P.col);
+      const int x0 = (local % mv.ntx) * VTW, y0 = (local / mv.ntx) * TH;
+      prefetch_tile<K, TH>(P, x0, y0);
+      const double rho_share = first ? 0.0 : part_share(pcg_partials(P, PART_RZ, m - 1), mv.nupd);
+      auto get_beta = [&]() -> float {
+        if (first) return 0.f;
+        const double rho = block_total(rho_share), rho_old = P.sc->rho2[(m - 1) & 1];
+        if (tid == 0 && local == 0) P.sc->rho2[m & 1] = rho;
+        return rho_old != 0.0 ? (float)(rho / rho_old) : 0.f;
+      };
+      float* p = const_cast<float*>(mv.p);
+      const float pq =
+          apply_tile<K, TH>(P, t, ct, x0, y0, 0, first, get_beta, p, p, P.q, maps + 2 * v, maps + 2 * v + 1);
+      const double bs = block_sum_f(pq);
+      if (tid == 0) pcg_partials(P, PART_PQ, m)[local] = bs;
+      __syncthreads();  // the next tile re-stages shared memory and the video record
+    }
+    if (!grid_sync(bar)) return;
+    const int last = m == m_inner ? 1 : 0;
+    // vector blocks of 256 items-strides, each done by this block's nth threads
+    for (int u = b; u < nupd; u += nb) {
+      int v;
+      const int local = multi_video<true>(vids, nv, mv, v, u);
+      const Params& P = mv.P;
+      const double pqs = block_total(part_share(pcg_partials(P, PART_PQ, m), mv.ntiles));
+      const float alpha = pqs != 0.0 ? (float)(P.sc->rho2[m & 1] / pqs) : 0.f;
+      float rz = 0.f;
+      for (int h = tid; h < 256; h += nth)
+        rz += update_range<K>(P, mv.p, alpha, last, (long)local * 256 + h, (long)mv.nupd * 256);
+      if (!last) {
+        const double bs = block_sum_f(rz);
+        if (tid == 0) pcg_partials(P, PART_RZ, m)[local] = bs;
+      }
+      __syncthreads();
+    }
+    if (last) break;
+    if (!grid_sync(bar)) return;
   }
 }
 

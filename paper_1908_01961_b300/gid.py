@@ -646,10 +646,11 @@ class Batch:
     def autotune(self, cache_path=None, reps=5):
         self._chk(self.lib.gid_batch_autotune(self.h, cache_path.encode() if cache_path else None, reps))
 
-    def set_worklist(self, on: bool):
-        """True: PCG steps as work-list launches over all videos of one K (default);
-        False: one graph branch per video."""
-        self._chk(self.lib.gid_batch_set_worklist(self.h, 1 if on else 0))
+    def set_worklist(self, on: bool, persistent: bool = False):
+        """True: PCG steps as work-list launches over all videos of one K (default), or with
+        persistent=True as one cooperative launch per K and Gauss-Newton step; False: one graph
+        branch per video."""
+        self._chk(self.lib.gid_batch_set_worklist(self.h, (2 if persistent else 1) if on else 0))
 
 
 class Net:

@@ -130,12 +130,12 @@ GROUPED = [dict(H=48, W=64, K=4, n_cells=12), dict(H=29, W=37, K=4, n_cells=7), 
            dict(H=30, W=33, K=3, n_cells=6), dict(H=75, W=131, K=3, n_cells=14)]
 
 
-def run_grouped(worklist, frames=2):
+def run_grouped(worklist, frames=2, persistent=False):
     from paper_1908_01961_b300 import gid
     cs = [Case(**sh, seed=20 + i, frames=frames, temporal=(i % 2 == 0)) for i, sh in enumerate(GROUPED)]
     weights = [gid.default_weights(c.off_s, c.off_t if c.temporal else None, temporal=int(c.temporal)) for c in cs]
     b = gid.Batch([(c.H, c.W, c.K) for c in cs], weights)
-    b.set_worklist(worklist)
+    b.set_worklist(worklist, persistent)
     for v, c in zip(b.videos, cs):
         v.set_base_colors(c.b_init)
         v.set_apply_tile(17)
@@ -187,3 +187,30 @@ def test_worklist_is_reproducible():
     _, b = run_grouped(True, frames=1)
     for (Xa, ba, _), (Xb, bb, _) in zip(a[0], b[0]):
         assert np.array_equal(Xa, Xb) and np.array_equal(ba, bb)
+
+
+def test_persistent_worklist_matches_worklist_and_oracle():
+    """The work list as one cooperative launch per K group and Gauss-Newton step
+    (grid barriers between the phases): against the launched work list (same
+    arithmetic up to the grouping of FP32 partials: state within 1e-3, energy
+    within 1e-4 relative) and, for both frames, against the oracle."""
+    cs, ps = run_grouped(True, persistent=True)
+    _, wl = run_grouped(True)
+    for t in range(2):
+        for (Xp, bp, Ep), (Xw, bw, Ew) in zip(ps[t], wl[t]):
+            assert np.abs(Xp - Xw).max() <= 1e-3
+            assert np.abs(bp - bw).max() <= 1e-3
+            assert Ep == pytest.approx(Ew, rel=1e-4)
+    for i, c in enumerate(cs):
+        pb = c.oracle_problem(0)
+        Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), 3, 6)
+        X, bc, E = ps[0][i]
+        assert np.abs(np.exp(X[:3]) - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(X[3:] - Xo[3:]).max() <= 1e-3
+        assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+        pb = c.oracle_problem(1, rprev=X[:3], b=bc) if c.temporal else c.oracle_problem(1, b=bc)
+        Xo, bo, hist = O.solve_frame(pb, X, 3, 6)
+        X1, _, E1 = ps[1][i]
+        assert np.abs(np.exp(X1[:3]) - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(X1[3:] - Xo[3:]).max() <= 1e-3
+        assert E1 == pytest.approx(hist[-1].sum(), rel=1e-4)
