@@ -214,3 +214,31 @@ def test_persistent_worklist_matches_worklist_and_oracle():
         assert np.abs(np.exp(X1[:3]) - np.exp(Xo[:3])).max() <= 1e-3
         assert np.abs(X1[3:] - Xo[3:]).max() <= 1e-3
         assert E1 == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+@pytest.mark.parametrize("persistent", [False, True])
+def test_worklist_degenerate_videos(persistent):
+    """Videos of one row, one column, narrower than a float4 chunk, and K = 1 and
+    10 in one work-list batch (each a group of its own or sharing one): one
+    frame 3 x 5 from the cold start against the oracle."""
+    from paper_1908_01961_b300 import gid
+    shapes = [dict(H=1, W=130, K=2, n_cells=3), dict(H=40, W=1, K=2, n_cells=3), dict(H=3, W=7, K=2, n_cells=2),
+              dict(H=30, W=40, K=1, n_cells=3), dict(H=30, W=40, K=10, n_cells=14)]
+    cs = [Case(**sh, seed=30 + i) for i, sh in enumerate(shapes)]
+    b = gid.Batch([(c.H, c.W, c.K) for c in cs], [gid.default_weights(c.off_s) for c in cs])
+    b.set_worklist(True, persistent)
+    for v, c in zip(b.videos, cs):
+        v.set_base_colors(c.b_init)
+    ins = [c.gpu_inputs(0) for c in cs]
+    b.set_frames([i[0] for i in ins], [i[1] for i in ins])
+    b.init(0)
+    b.run(3, 5)
+    for v, c in zip(b.videos, cs):
+        R, T = v.layers()
+        E, _ = v.energy()
+        pb = c.oracle_problem(0)
+        Xo, bo, hist = O.solve_frame(pb, pb.init_cold(), 3, 5)
+        assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
+        assert np.abs(v.base_colors() - bo).max() <= 1e-3
+        assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
