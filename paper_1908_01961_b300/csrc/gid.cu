@@ -1472,11 +1472,14 @@ extern "C" int gid_get_pcg_layout(gid_ctx* c, int* rows, int* tile_w, int* tile_
 // ---------------------------------------------------------------- L2 persistence of the coefficients
 
 // Contexts of this process whose launches carry a window (the set-aside is
-// released when the last one turns it off or is destroyed).
+// released when the last one turns it off or is destroyed); the count and the
+// device limit are changed under one lock.
 static int g_l2_users = 0;
+static std::mutex g_l2_mu;
 
 static void l2_release(gid_ctx* c) {
   if (!c->l2_window) return;
+  std::lock_guard<std::mutex> lock(g_l2_mu);
   c->l2_window = false;
   if (--g_l2_users == 0) {
     cudaCtxResetPersistingL2Cache();
@@ -1509,6 +1512,7 @@ extern "C" int gid_set_l2_window(gid_ctx* c, int on) {
   if (bytes > (size_t)maxp || bytes > (size_t)maxw)
     return fail(c, GID_ERR_INVALID_ARG, "the coefficient planes exceed the device's persisting L2");
   const size_t win = bytes;
+  std::lock_guard<std::mutex> lock(g_l2_mu);
   size_t cur = 0;
   GID_TRY_CUDA(c, cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
   const size_t want = std::min(win, (size_t)maxp);
@@ -2086,7 +2090,9 @@ extern "C" int gid_batch_run(gid_batch* b, int n_outer, int m_inner) {
     if (wl && !build_worklist(b, groups, tables)) {
       cudaGetLastError();
       for (void* p : tables) cudaFree(p);
-      return bfail(b, GID_ERR_CUDA, "batch work-list tables");
+      return bfail(b, GID_ERR_CUDA,
+                   b->persistent_wl ? "batch work-list tables, or the persistent work list cannot be co-scheduled"
+                                    : "batch work-list tables");
     }
     GID_BTRY(b, cudaStreamBeginCapture(b->bs, cudaStreamCaptureModeThreadLocal));
     int rc = GID_OK;

@@ -178,3 +178,22 @@ def test_fused_full_size_640x480_K6_pcg_delta():
     delta = s.stage_pcg(cfg["M"])
     ref, _ = case.oracle_problem().pcg(X, cfg["M"])
     close(delta.cpu().numpy(), ref, 1e-4, "PCG delta at 640x480")
+
+
+@pytest.mark.parametrize("rows", [8, 17])
+def test_fused_pcg_delta_k8(rows):
+    """K = 8: at 17 rows the two staged tiles do not fit in shared memory, so the
+    halo's M^-1 q comes from global memory (four chunks in flight per thread);
+    at 8 rows both are staged.  PCG delta and rho history after 10 steps
+    against the oracle."""
+    case = Case(H=57, W=150, K=8, n_cells=10, seed=5)
+    s = fused_solver(case, rows)
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    pb = case.oracle_problem()
+    X = random_state(pb, 2)
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    delta = s.stage_pcg(10)
+    ref, rho = pb.pcg(X, 10)
+    close(delta.cpu().numpy(), ref, 1e-4, f"fused PCG delta K=8, {rows} rows")
+    np.testing.assert_allclose(s.pcg_history(), rho[:10], rtol=1e-4, atol=1e-4 * rho[0])
