@@ -372,3 +372,16 @@ def test_k8_pcg_delta_each_tile_shape(rows):
     delta = s.stage_pcg(10)
     ref, _ = pb.pcg(X, 10)
     close(delta.cpu().numpy(), ref, tol=1e-4, what=f"PCG delta K=8, {rows} rows")
+
+
+def test_default_tile_by_frame_size():
+    """A new context starts on 128 x 17 tiles where they fit in one wave (at most
+    one per SM: 640 x 480 is 145 tiles), else on 128 x 4 tiles (1920 x 1080)."""
+    from paper_1908_01961_b300 import gid
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    small = gid.Solver(480, 640, 6, gid.default_weights())
+    big = gid.Solver(1080, 1920, 8, gid.default_weights())
+    assert small.pcg_layout()[0] == (17 if 5 * 29 <= sms else 4)
+    assert big.pcg_layout()[0] == 4
+    small.close()
+    big.close()
