@@ -242,3 +242,33 @@ def test_worklist_degenerate_videos(persistent):
         assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
         assert np.abs(v.base_colors() - bo).max() <= 1e-3
         assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+def test_worklist_full_size_classes_one_outer_iteration():
+    """One video of each of the 24-video benchmark's size classes (320x240,
+    640x480, 960x540, 1280x720; K = 4, 6, 8, 4), in the work-list launch
+    configuration the benchmark times: one outer iteration (a Gauss-Newton step
+    of 20 PCG steps and the base-colour step) from the GPU's initial state, each
+    against the oracle's from the same state: layers within 1e-3 max-abs, the
+    base colours within 1e-3, the energy within 1e-4 relative."""
+    from paper_1908_01961_b300 import gid
+    shapes = [dict(H=240, W=320, K=4, n_cells=20), dict(H=480, W=640, K=6, n_cells=40),
+              dict(H=540, W=960, K=8, n_cells=60), dict(H=720, W=1280, K=4, n_cells=80)]
+    cs = [Case(**sh, seed=40 + i) for i, sh in enumerate(shapes)]
+    b = gid.Batch([(c.H, c.W, c.K) for c in cs], [gid.default_weights(c.off_s) for c in cs])
+    for v, c in zip(b.videos, cs):
+        v.set_base_colors(c.b_init)
+    ins = [c.gpu_inputs(0) for c in cs]
+    b.set_frames([i[0] for i in ins], [i[1] for i in ins])
+    b.init(0)
+    X0 = [v.state().cpu().numpy().astype(np.float64) for v in b.videos]
+    b.run(1, 20)
+    for v, c, x0 in zip(b.videos, cs, X0):
+        R, T = v.layers()
+        E, _ = v.energy()
+        pb = c.oracle_problem(0)
+        Xo, bo, hist = O.solve_frame(pb, x0, 1, 20)
+        assert np.abs(R.cpu().numpy() - np.exp(Xo[:3])).max() <= 1e-3
+        assert np.abs(T.cpu().numpy() - Xo[3:]).max() <= 1e-3
+        assert np.abs(v.base_colors() - bo).max() <= 1e-3
+        assert E == pytest.approx(hist[-1].sum(), rel=1e-4)
