@@ -560,6 +560,26 @@ def run_gid(args, ws, rank, local):
                 Ei, _ = sp.energy()
                 preconditioners.append({"preconditioner": kind, "N": N, "M": Mi, "ms": float(np.median(times)),
                                         "energy": Ei})
+        # Jacobi with the single-reduction recurrence (one grid-wide reduction per PCG
+        # step): the fused step at the same tile height
+        sp.set_preconditioner("jacobi")
+        rows_f = (tile_rows & 255) if tile_rows and tile_rows > 0 else 17
+        sp.set_apply_tile((17 if rows_f == 16 else rows_f) | gid.FUSED)   # the fused step has no 16-row tile
+        for Mi in (10, 15, 20):
+            times = []
+            for rep in range(4):
+                sp.set_base_colors(b0)
+                sp.init(0)
+                a0, a1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a0.record(stream)
+                sp.run(N, Mi)
+                a1.record(stream)
+                torch.cuda.synchronize()
+                if rep > 0:
+                    times.append(a0.elapsed_time(a1))
+            Ei, _ = sp.energy()
+            preconditioners.append({"preconditioner": "jacobi, single-reduction recurrence (fused step)", "N": N,
+                                    "M": Mi, "ms": float(np.median(times)), "energy": Ei})
         sp.close()
 
     # the same video with the block-Jacobi preconditioner at equal final energy: the

@@ -194,3 +194,36 @@ def test_batch_uses_each_contexts_preconditioner():
         assert v.preconditioner() == "block"
         assert np.array_equal(v.state().cpu().numpy(), X)
         assert np.array_equal(v.base_colors(), bc)
+
+
+@pytest.mark.parametrize("name", list(CASES))
+@pytest.mark.parametrize("loop", ["fused", "resident"])
+def test_single_reduction_pcg_matches_its_oracle_recurrence(name, loop):
+    """The single-reduction (one grid-wide reduction per PCG step) recurrence on
+    the GPU, as the fused step and as the resident loop run it, against the
+    oracle's single-reduction variant: PCG delta after 10 steps within 1e-4 of
+    its max, and the rho history within 1e-4; the oracle's two recurrences agree
+    in exact arithmetic, so the GPU is also within the bar of the textbook one."""
+    from paper_1908_01961_b300 import gid
+    case = Case(**CASES[name], seed=3)
+    s = case.solver()
+    if loop == "fused":
+        s.set_apply_tile(17 | gid.FUSED)
+    else:
+        try:
+            s.set_apply_tile(gid.RESIDENT)
+        except gid.GidError as e:
+            assert e.code == gid.ERR_INVALID_ARG
+            pytest.skip("the resident loop does not fit this frame on this device")
+    rgb, lab = case.gpu_inputs()
+    s.set_frame(rgb, lab)
+    pb = case.oracle_problem()
+    X = random_state(pb, 5)
+    s.set_state(torch.from_numpy(X.astype(np.float32)).cuda())
+    delta = s.stage_pcg(10).cpu().numpy()
+    ref, rz = pb.pcg_variant(X, 10, single_reduction=True)
+    err = np.abs(delta - ref).max()
+    assert err <= 1e-4 * np.abs(ref).max(), f"max err {err:.3e} vs {np.abs(ref).max():.3e}"
+    np.testing.assert_allclose(s.pcg_history(), rz[:10], rtol=1e-4, atol=1e-4 * rz[0])
+    textbook, _ = pb.pcg(X, 10)
+    assert np.abs(delta - textbook).max() <= 1e-4 * np.abs(textbook).max()
