@@ -73,3 +73,37 @@ def test_stream_1920x1080_K8_stages_and_one_outer_iteration():
     assert np.abs(T1.cpu().numpy() - X1[3:]).max() <= 1e-3
     assert np.abs(s.base_colors() - b1).max() <= 1e-3
     assert E1 == pytest.approx(hist[-1].sum(), rel=1e-4)
+
+
+def test_1920x1080_K10_stages_and_one_outer_iteration():
+    """The largest frame of the workloads with the largest K (GID_MAX_K = 10: 14
+    unknowns and 49 coefficient planes per pixel), no temporal pairs: every stage
+    at the GPU's cold-start state, then one outer iteration from it, at the same
+    bars as above."""
+    cfg = synth.STREAM_1080P
+    M = cfg["M"]
+    case = Case(cfg["H"], cfg["W"], 10, cfg["n_cells"], seed=6)
+    s = case.solver()
+    rgb, lab = case.gpu_inputs(0)
+    s.set_frame(rgb, lab)
+    s.init(0)
+    X0 = s.state().cpu().numpy().astype(np.float64)
+    pb = case.oracle_problem(0)
+    g, d = s.stage_linearize()
+    close(g.cpu().numpy(), pb.rhs(X0), 2e-5, "-J^T F")
+    close(d.cpu().numpy(), pb.diag(X0), 2e-5, "diag J^T J")
+    p = np.random.default_rng(2).normal(size=X0.shape).astype(np.float32)
+    q = s.stage_apply(torch.from_numpy(p).cuda())
+    close(q.cpu().numpy(), pb.apply(X0, p.astype(np.float64)), 2e-5, "J^T J p")
+    A, gb = s.stage_dense_normal()
+    Ao, go = pb.dense_normal(X0)
+    close(A, Ao, 1e-5, "A")
+    close(gb, go, 1e-4, "g")
+    s.run(1, M)
+    R1, T1 = s.layers()
+    E1, _ = s.energy()
+    X1, b1, hist = O.solve_frame(pb, X0, 1, M)
+    assert np.abs(R1.cpu().numpy() - np.exp(X1[:3])).max() <= 1e-3
+    assert np.abs(T1.cpu().numpy() - X1[3:]).max() <= 1e-3
+    assert np.abs(s.base_colors() - b1).max() <= 1e-3
+    assert E1 == pytest.approx(hist[-1].sum(), rel=1e-4)
