@@ -275,14 +275,18 @@ int gid_set_apply_tile(gid_ctx* ctx, int rows);
 
 /* on != 0: the PCG launches (operator, vector and fused steps) carry an L2
  * access-policy window over the operator coefficient planes (NC planes, written
- * once per Gauss-Newton step and read by every PCG step of it): accesses to them
+ * once per Gauss-Newton step and read by every PCG step of it) and as many of
+ * the PCG vectors q, p and z (in that order) as fit with them: accesses to them
  * are marked persisting, up to the device's persisting-L2 limit, which the
- * first context to turn this on raises to the planes' size (capped by the
+ * first context to turn this on raises to the window's size (capped by the
  * device maximum) for this process; the set-aside is released when the last
- * context turns it off or is destroyed.  Only speed changes.  Synchronises and
- * drops the context's cached graphs.  GID_ERR_INVALID_ARG if the device has no
- * persisting L2 or the planes do not fit in its maximum set-aside whole (a
- * partial window thrashes it: 1920 x 1080 K = 8 ran 52 % slower with one).
+ * context turns it off or is destroyed; while it is held, the rest of the L2
+ * is all that other work on the device (other contexts, batches) can use.  Only
+ * speed changes.  Synchronises and drops the context's cached graphs.
+ * GID_ERR_INVALID_ARG if the device has no persisting L2 or the coefficient
+ * planes alone do not fit in its maximum
+ * set-aside (a partial window thrashes it: 1920 x 1080 K = 8 ran 52 % slower
+ * with one).
  * gid_autotune times its chosen loop with and without the window and keeps the
  * faster. */
 int gid_set_l2_window(gid_ctx* ctx, int on);

@@ -739,13 +739,17 @@ extern "C" int gid_create(int H, int W, int K, const gid_weights* w, void* strea
   c->ws = planes(ns);
   c->wt = planes(nt);
   c->wtsum = planes(1);
+  // z, p, q and the coefficients last and contiguous: the PCG loop re-reads them
+  // every step, and one L2 window (gid_set_l2_window) covers the coefficients and
+  // as many of q, p, z as fit (at 640 x 480 K = 6: p and q; p and q in the window
+  // measured 35.4 us per PCG step, z and q 35.8, the coefficients alone 37.4)
   c->X = planes(c->V);
   c->d = planes(c->V);
+  c->pB = planes(c->V);
+  c->Minv = planes(c->V);
   c->z = planes(c->V);
   c->pA = planes(c->V);
-  c->pB = planes(c->V);
   c->q = planes(c->V);
-  c->Minv = planes(c->V);
   c->coef = planes(coef_planes(K, w->n_spatial_pairs));
   c->lab = (uint8_t*)take(lbytes);
   c->col = (DevColors*)take(sizeof(DevColors));
@@ -1507,18 +1511,28 @@ extern "C" int gid_set_l2_window(gid_ctx* c, int on) {
   GID_TRY_CUDA(c, cudaDeviceGetAttribute(&maxp, cudaDevAttrMaxPersistingL2CacheSize, dev));
   GID_TRY_CUDA(c, cudaDeviceGetAttribute(&maxw, cudaDevAttrMaxAccessPolicyWindowSize, dev));
   if (maxp <= 0 || maxw <= 0) return fail(c, GID_ERR_INVALID_ARG, "no persisting L2 on this device");
-  const size_t bytes = sizeof(float) * (size_t)coef_planes(c->K, c->w.n_spatial_pairs) * c->plane;
-  // a window the set-aside cannot hold whole thrashes it (measured slower than none)
-  if (bytes > (size_t)maxp || bytes > (size_t)maxw)
+  // the coefficients and as many of q, p and z (allocated just before them, in that
+  // order backwards) as fit; a window the set-aside cannot hold whole thrashes it
+  // (measured slower than none)
+  const char* coef_end = reinterpret_cast<const char*>(c->coef) +
+                         sizeof(float) * (size_t)coef_planes(c->K, c->w.n_spatial_pairs) * c->plane;
+  const float* starts[4] = {c->z, c->pA, c->q, c->coef};  // consecutive in the pool
+  const char* base = nullptr;
+  size_t win = 0;
+  for (const float* s0 : starts) {
+    base = reinterpret_cast<const char*>(s0);
+    win = (size_t)(coef_end - base);
+    if (win <= (size_t)maxp && win <= (size_t)maxw) break;
+  }
+  if (win > (size_t)maxp || win > (size_t)maxw)
     return fail(c, GID_ERR_INVALID_ARG, "the coefficient planes exceed the device's persisting L2");
-  const size_t win = bytes;
   std::lock_guard<std::mutex> lock(g_l2_mu);
   size_t cur = 0;
   GID_TRY_CUDA(c, cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
   const size_t want = std::min(win, (size_t)maxp);
   if (cur < want) GID_TRY_CUDA(c, cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, want));
   GID_TRY_CUDA(c, cudaDeviceGetLimit(&cur, cudaLimitPersistingL2CacheSize));
-  c->l2win.base_ptr = c->coef;
+  c->l2win.base_ptr = const_cast<char*>(base);
   c->l2win.num_bytes = win;
   c->l2win.hitRatio = std::min(1.0f, (float)cur / (float)win);
   c->l2win.hitProp = cudaAccessPropertyPersisting;
